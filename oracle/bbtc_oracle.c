@@ -1,0 +1,395 @@
+/*
+ * bbtc_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU restatement of block-based triangle
+ * counting (bbTC, Yasar, Rajamanickam, Berry & Catalyurek, arXiv 2009.12457).
+ * Only the test suite, the package smoke check and the benchmark's CPU
+ * baseline leg may call this file; the CUDA library shares no code with it.
+ *
+ * Every quantity is an integer except the task-order estimate (Sec. 5), which
+ * is only used to order work. Steps follow the paper's order:
+ *
+ *   canonical simple edge set  (Sec. 2: simple undirected G=(V,E), (u,v) with u<v)
+ *   degree                     (Sec. 2, Sec. 4.1)
+ *   order by degree            (Sec. 4.1: non-decreasing degree order)
+ *   orientation                (Sec. 2: N(G,u) = {v : (u,v) in E, u < v})
+ *   partition / cuts           (Sec. 2 vertex partition V^p; Sec. 4.1)
+ *   block sizes |G_ij|         (Sec. 2 G_ij; Sec. 4.4 lambda)
+ *   task composition           (Sec. 4.2, Alg. 4)
+ *   task estimate + order      (Sec. 5, ExecTime)
+ *   per-task count             (Sec. 4.3, Alg. 5 bbTC-Intersect, Alg. 6 bbTC-HMap)
+ *   whole-graph count          (Sec. 3, Alg. 2 TC-Intersect with Alg. 1, Alg. 3 TC-HMap)
+ *
+ * Readings of the paper taken here (each is also listed in the design notes):
+ *  - Alg. 1 compares A[b] = B[b] in its first branch; the intended test is
+ *    A[a] = B[b] (the algorithm counts common elements of two sorted lists).
+ *  - The degree used for ordering is the undirected simple-graph degree.
+ *  - Ties in degree are broken by the original vertex id, ascending.
+ *  - Edges point from the lower to the higher position in the degree order.
+ *  - The partition is contiguous in that order: c_0 = 0, c_p = n and, for
+ *    0 < i < p, c_i = min{ r : rowptr[r] >= ceil(i*m/p) } on the oriented CSR.
+ *  - Alg. 3 / Alg. 6 leave H's initial value unstated; here it is -1.
+ *  - ExecTime(t) = |G_ij| * max(delta(G_ik), delta(G_jk)), delta(G_ab) =
+ *    |G_ab| / |V_a| (0 when V_a is empty); ties keep Alg. 4's order.
+ *
+ * Parity pins (tests, not this file): brute force over all vertex triples,
+ * trace(A^3)/6, closed forms (K_n, wheels, friendship, complete tripartite,
+ * bipartite/grid/tree = 0), sum of per-vertex counts = 3T, the task count
+ * p(p+1)(p+2)/6 against the paper's tiles/tasks table, and agreement of the
+ * two whole-graph and the two per-task algorithms.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- helpers */
+
+static int cmp_u64(const void *x, const void *y) {
+  uint64_t a = *(const uint64_t *)x, b = *(const uint64_t *)y;
+  return (a > b) - (a < b);
+}
+
+/* first index in [lo, hi) of sorted list L whose value is >= x */
+static int64_t lower_bound_i32(const int32_t *L, int64_t lo, int64_t hi, int64_t x) {
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if ((int64_t)L[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+/* ------------------------------------------------ canonical simple edges */
+
+/*
+ * Sec. 2 treats G as a simple undirected graph and writes each edge (u,v) with
+ * u < v. Input: any CSR listing an edge in one or both directions, possibly
+ * with duplicates and self-loops. Output: the sorted set of keys
+ * (min << 32) | max over entries with endpoints that differ. keys_out must hold
+ * rowptr[n] entries. Returns m, the number of simple undirected edges.
+ */
+int64_t orc_canonical_edges(int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                            uint64_t *keys_out) {
+  int64_t cnt = 0;
+  for (int64_t u = 0; u < n; ++u) {
+    for (int64_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+      int64_t v = colidx[e];
+      if (v == u) continue;
+      uint64_t a = (uint64_t)(u < v ? u : v), b = (uint64_t)(u < v ? v : u);
+      keys_out[cnt++] = (a << 32) | b;
+    }
+  }
+  qsort(keys_out, (size_t)cnt, sizeof(uint64_t), cmp_u64);
+  int64_t m = 0;
+  for (int64_t i = 0; i < cnt; ++i)
+    if (i == 0 || keys_out[i] != keys_out[i - 1]) keys_out[m++] = keys_out[i];
+  return m;
+}
+
+/* Undirected simple degree of every vertex (reading of the ordering degree). */
+void orc_degree(int64_t n, int64_t m, const uint64_t *keys, int64_t *deg) {
+  memset(deg, 0, sizeof(int64_t) * (size_t)n);
+  for (int64_t e = 0; e < m; ++e) {
+    deg[keys[e] >> 32] += 1;
+    deg[keys[e] & 0xFFFFFFFFULL] += 1;
+  }
+}
+
+/* ------------------------------------------------------- order by degree */
+
+static const int64_t *g_sort_deg; /* comparator context (single-threaded) */
+
+static int cmp_by_degree(const void *x, const void *y) {
+  int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+  if (g_sort_deg[a] != g_sort_deg[b]) return g_sort_deg[a] < g_sort_deg[b] ? -1 : 1;
+  return (a > b) - (a < b);
+}
+
+/*
+ * Sec. 4.1: vertices re-ordered in non-decreasing degree order. perm[r] is the
+ * original id at position r; rank[v] is the position of original vertex v.
+ */
+void orc_order_by_degree(int64_t n, const int64_t *deg, int32_t *rank, int32_t *perm) {
+  for (int64_t v = 0; v < n; ++v) perm[v] = (int32_t)v;
+  g_sort_deg = deg;
+  qsort(perm, (size_t)n, sizeof(int32_t), cmp_by_degree);
+  g_sort_deg = NULL;
+  for (int64_t r = 0; r < n; ++r) rank[perm[r]] = (int32_t)r;
+}
+
+/* ------------------------------------------------------------ orientation */
+
+/*
+ * Sec. 2: with vertices named by their position in the order, each edge is
+ * stored once as (u,v) with u < v and N(G,u) = {v : (u,v) in E, u < v}.
+ * Output: oriented CSR in position space, each row sorted ascending.
+ * rowptr_out has n+1 entries, colidx_out m.
+ */
+void orc_orient(int64_t n, int64_t m, const uint64_t *keys, const int32_t *rank,
+                int64_t *rowptr_out, int32_t *colidx_out) {
+  uint64_t *ok = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(m > 0 ? m : 1));
+  for (int64_t e = 0; e < m; ++e) {
+    uint64_t ra = (uint64_t)rank[keys[e] >> 32];
+    uint64_t rb = (uint64_t)rank[keys[e] & 0xFFFFFFFFULL];
+    ok[e] = ra < rb ? (ra << 32) | rb : (rb << 32) | ra;
+  }
+  qsort(ok, (size_t)m, sizeof(uint64_t), cmp_u64);
+  memset(rowptr_out, 0, sizeof(int64_t) * (size_t)(n + 1));
+  for (int64_t e = 0; e < m; ++e) rowptr_out[(ok[e] >> 32) + 1] += 1;
+  for (int64_t u = 0; u < n; ++u) rowptr_out[u + 1] += rowptr_out[u];
+  for (int64_t e = 0; e < m; ++e) colidx_out[e] = (int32_t)(ok[e] & 0xFFFFFFFFULL);
+  free(ok);
+}
+
+/* --------------------------------------------- whole-graph counts (Sec. 3) */
+
+/* Alg. 1 (nIntersect), with the first comparison read as A[a] = B[b]. */
+uint64_t orc_n_intersect(const int32_t *A, int64_t na, const int32_t *B, int64_t nb) {
+  int64_t a = 0, b = 0;
+  uint64_t c = 0;
+  while (a < na && b < nb) {
+    if (A[a] == B[b]) { ++c; ++a; ++b; }
+    else if (A[a] < B[b]) ++a;
+    else ++b;
+  }
+  return c;
+}
+
+/* Alg. 2 (TC-Intersect) over the oriented CSR. */
+uint64_t orc_tc_intersect(int64_t n, const int64_t *rp, const int32_t *ci) {
+  uint64_t tau = 0;
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+      int64_t v = ci[e];
+      tau += orc_n_intersect(ci + rp[u], rp[u + 1] - rp[u], ci + rp[v], rp[v + 1] - rp[v]);
+    }
+  return tau;
+}
+
+/* Alg. 3 (TC-HMap) over the oriented CSR; H starts at -1 for every vertex. */
+uint64_t orc_tc_hmap(int64_t n, const int64_t *rp, const int32_t *ci) {
+  int64_t *H = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t v = 0; v < n; ++v) H[v] = -1;
+  uint64_t tau = 0;
+  for (int64_t u = 0; u < n; ++u) {
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) H[ci[e]] = u;
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+      int64_t v = ci[e];
+      for (int64_t f = rp[v]; f < rp[v + 1]; ++f)
+        if (H[ci[f]] == u) ++tau;
+    }
+  }
+  free(H);
+  return tau;
+}
+
+/*
+ * Per-vertex triangle counts in ORIGINAL ids: every triangle found by Alg. 2's
+ * loops adds one to each of its three corners. perm maps positions to ids.
+ */
+void orc_per_vertex(int64_t n, const int64_t *rp, const int32_t *ci, const int32_t *perm,
+                    uint64_t *cnt_out) {
+  memset(cnt_out, 0, sizeof(uint64_t) * (size_t)n);
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+      int64_t v = ci[e];
+      int64_t a = rp[u], b = rp[v];
+      while (a < rp[u + 1] && b < rp[v + 1]) {
+        if (ci[a] == ci[b]) {
+          cnt_out[perm[u]] += 1; cnt_out[perm[v]] += 1; cnt_out[perm[ci[a]]] += 1;
+          ++a; ++b;
+        } else if (ci[a] < ci[b]) ++a;
+        else ++b;
+      }
+    }
+}
+
+/* ------------------------------------------------------------- partition */
+
+/*
+ * Contiguous partition of the ordered vertices into p parts balanced on
+ * oriented edges: c_0 = 0, c_p = n, c_i = min{ r : rowptr[r] >= ceil(i*m/p) }.
+ */
+void orc_cuts(int64_t n, const int64_t *rp, int32_t p, int32_t *cuts) {
+  int64_t m = rp[n];
+  cuts[0] = 0;
+  cuts[p] = (int32_t)n;
+  for (int32_t i = 1; i < p; ++i) {
+    int64_t target = (i * m + p - 1) / p;
+    int64_t r = 0;
+    while (r < n && rp[r] < target) ++r;
+    cuts[i] = (int32_t)r;
+  }
+}
+
+/* Part index of position r: the i with c_i <= r < c_{i+1}. */
+static int32_t part_of(int64_t r, int32_t p, const int32_t *cuts) {
+  int32_t i = 0;
+  /* empty parts (c_i = c_{i+1}) own nothing: stop at the first c_{i+1} > r */
+  while (i + 1 < p && cuts[i + 1] <= r) ++i;
+  return i;
+}
+
+/* |G_ij| for all (i,j) in row-major p*p order (Sec. 2 definition of G_ij). */
+void orc_block_nnz(int64_t n, const int64_t *rp, const int32_t *ci, int32_t p,
+                   const int32_t *cuts, int64_t *nnz) {
+  memset(nnz, 0, sizeof(int64_t) * (size_t)p * (size_t)p);
+  for (int64_t u = 0; u < n; ++u) {
+    int32_t i = part_of(u, p, cuts);
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) nnz[(int64_t)i * p + part_of(ci[e], p, cuts)] += 1;
+  }
+}
+
+/* ------------------------------------------------------- task composition */
+
+/* Sec. 4.2: |T| = p(p+1)(p+2)/6. */
+int64_t orc_num_tasks(int32_t p) {
+  return (int64_t)p * (p + 1) * (p + 2) / 6;
+}
+
+/* Alg. 4: every (i,j,k) with i <= j <= k, in the order of its three loops. */
+int64_t orc_task_list(int32_t p, int32_t *ti, int32_t *tj, int32_t *tk) {
+  int64_t t = 0;
+  for (int32_t i = 0; i < p; ++i)
+    for (int32_t j = i; j < p; ++j)
+      for (int32_t k = j; k < p; ++k) { ti[t] = i; tj[t] = j; tk[t] = k; ++t; }
+  return t;
+}
+
+/* Sec. 5 task estimate: ExecTime(t) = |G_ij| * max(delta(G_ik), delta(G_jk)). */
+void orc_exec_time(int32_t p, const int32_t *cuts, const int64_t *nnz, double *est) {
+  int64_t t = 0;
+  for (int32_t i = 0; i < p; ++i)
+    for (int32_t j = i; j < p; ++j)
+      for (int32_t k = j; k < p; ++k) {
+        int64_t vi = cuts[i + 1] - cuts[i], vj = cuts[j + 1] - cuts[j];
+        double dik = vi > 0 ? (double)nnz[(int64_t)i * p + k] / (double)vi : 0.0;
+        double djk = vj > 0 ? (double)nnz[(int64_t)j * p + k] / (double)vj : 0.0;
+        est[t++] = (double)nnz[(int64_t)i * p + j] * (dik > djk ? dik : djk);
+      }
+}
+
+static const double *g_sort_est;
+
+static int cmp_by_estimate(const void *x, const void *y) {
+  int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+  if (g_sort_est[a] != g_sort_est[b]) return g_sort_est[a] > g_sort_est[b] ? -1 : 1;
+  return (a > b) - (a < b);
+}
+
+/* Tasks in non-increasing estimate; equal estimates keep Alg. 4's order. */
+void orc_order_tasks(int64_t nt, const double *est, int32_t *order) {
+  for (int64_t t = 0; t < nt; ++t) order[t] = (int32_t)t;
+  g_sort_est = est;
+  qsort(order, (size_t)nt, sizeof(int32_t), cmp_by_estimate);
+  g_sort_est = NULL;
+}
+
+/* ------------------------------------------------- per-task counts (Sec. 4.3) */
+
+/* N(G_ab, u): the part of u's sorted row whose columns lie in V_b. */
+static void partial_list(const int64_t *rp, const int32_t *ci, int64_t u, int32_t b,
+                         const int32_t *cuts, int64_t *lo, int64_t *hi) {
+  *lo = lower_bound_i32(ci, rp[u], rp[u + 1], cuts[b]);
+  *hi = lower_bound_i32(ci, *lo, rp[u + 1], cuts[b + 1]);
+}
+
+/* Alg. 5 (bbTC-Intersect) for task (i,j,k). */
+uint64_t orc_bbtc_intersect_task(int64_t n, const int64_t *rp, const int32_t *ci,
+                                 const int32_t *cuts, int32_t i, int32_t j, int32_t k) {
+  (void)n;
+  uint64_t tau = 0;
+  for (int64_t u = cuts[i]; u < cuts[i + 1]; ++u) {
+    int64_t ij_lo, ij_hi, ik_lo, ik_hi;
+    partial_list(rp, ci, u, j, cuts, &ij_lo, &ij_hi);
+    partial_list(rp, ci, u, k, cuts, &ik_lo, &ik_hi);
+    for (int64_t e = ij_lo; e < ij_hi; ++e) {
+      int64_t v = ci[e], jk_lo, jk_hi;
+      partial_list(rp, ci, v, k, cuts, &jk_lo, &jk_hi);
+      tau += orc_n_intersect(ci + ik_lo, ik_hi - ik_lo, ci + jk_lo, jk_hi - jk_lo);
+    }
+  }
+  return tau;
+}
+
+/* Alg. 6 (bbTC-HMap) for task (i,j,k); H spans V_k and starts at -1. */
+uint64_t orc_bbtc_hmap_task(int64_t n, const int64_t *rp, const int32_t *ci,
+                            const int32_t *cuts, int32_t i, int32_t j, int32_t k) {
+  (void)n;
+  int64_t vk = cuts[k + 1] - cuts[k];
+  int64_t *H = (int64_t *)malloc(sizeof(int64_t) * (size_t)(vk > 0 ? vk : 1));
+  for (int64_t x = 0; x < vk; ++x) H[x] = -1;
+  uint64_t tau = 0;
+  for (int64_t u = cuts[i]; u < cuts[i + 1]; ++u) {
+    int64_t ik_lo, ik_hi, ij_lo, ij_hi;
+    partial_list(rp, ci, u, k, cuts, &ik_lo, &ik_hi);
+    for (int64_t e = ik_lo; e < ik_hi; ++e) H[ci[e] - cuts[k]] = u;
+    partial_list(rp, ci, u, j, cuts, &ij_lo, &ij_hi);
+    for (int64_t e = ij_lo; e < ij_hi; ++e) {
+      int64_t v = ci[e], jk_lo, jk_hi;
+      partial_list(rp, ci, v, k, cuts, &jk_lo, &jk_hi);
+      for (int64_t f = jk_lo; f < jk_hi; ++f)
+        if (H[ci[f] - cuts[k]] == u) ++tau;
+    }
+  }
+  free(H);
+  return tau;
+}
+
+/*
+ * Every triangle u < v < w (positions) lies in exactly one task:
+ * (part(u), part(v), part(w)), i <= j <= k because parts are contiguous
+ * (Sec. 4.2). This classifies the triangles found by a whole-graph merge and
+ * accumulates one count per task, indexed in Alg. 4 order.
+ */
+void orc_classify_triangles(int64_t n, const int64_t *rp, const int32_t *ci, int32_t p,
+                            const int32_t *cuts, uint64_t *per_task) {
+  int64_t nt = orc_num_tasks(p);
+  memset(per_task, 0, sizeof(uint64_t) * (size_t)nt);
+  /* index of (i,j,k) in Alg. 4 order, tabulated by enumeration */
+  int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)p * p * p);
+  int64_t t = 0;
+  for (int32_t i = 0; i < p; ++i)
+    for (int32_t j = i; j < p; ++j)
+      for (int32_t k = j; k < p; ++k) idx[((int64_t)i * p + j) * p + k] = t++;
+  for (int64_t u = 0; u < n; ++u) {
+    int32_t bu = part_of(u, p, cuts);
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+      int64_t v = ci[e];
+      int32_t bv = part_of(v, p, cuts);
+      int64_t a = rp[u], b = rp[v];
+      while (a < rp[u + 1] && b < rp[v + 1]) {
+        if (ci[a] == ci[b]) {
+          per_task[idx[((int64_t)bu * p + bv) * p + part_of(ci[a], p, cuts)]] += 1;
+          ++a; ++b;
+        } else if (ci[a] < ci[b]) ++a;
+        else ++b;
+      }
+    }
+  }
+  free(idx);
+}
+
+/* ------------------------------------------------------- workload figures */
+
+/*
+ * Algorithmic bytes of the counting step on the oriented CSR, with 4-byte ids:
+ *   wmin   = 4 * (m + sum over oriented edges (u,v) of d+(v))
+ *            (each edge read once, and the out-list of v read once per edge
+ *             that enters v -- the candidates that may close a wedge)
+ *   wmerge = 4 * sum over oriented edges (u,v) of (d+(u) + d+(v))
+ *   wedges = sum over oriented edges (u,v) of d+(v)
+ */
+void orc_work_figures(int64_t n, const int64_t *rp, const int32_t *ci, uint64_t *wmin,
+                      uint64_t *wmerge, uint64_t *wedges) {
+  uint64_t m = (uint64_t)rp[n], w = 0, mg = 0;
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+      int64_t v = ci[e];
+      uint64_t dv = (uint64_t)(rp[v + 1] - rp[v]), du = (uint64_t)(rp[u + 1] - rp[u]);
+      w += dv;
+      mg += du + dv;
+    }
+  *wmin = 4 * (m + w);
+  *wmerge = 4 * mg;
+  *wedges = w;
+}

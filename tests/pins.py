@@ -1,0 +1,198 @@
+"""Independent pins for the oracle: facts fixed by the paper or by mathematics.
+
+``pin_battery()`` runs a compact set of checks against whatever oracle build is
+active and returns the list of failures. The pin tests run it on the oracle
+itself (expecting none) and on deliberately broken copies of it (expecting at
+least one), so every pin below is shown to catch a plausible mistake.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import oracle
+from tests import graphs as G
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load_table4_pairs():
+    rows = []
+    with open(os.path.join(GOLDEN, "table4_tiles_tasks.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                tiles, tasks = (int(x) for x in line.split())
+                rows.append((tiles, tasks))
+    return rows
+
+
+def load_toy_tasks():
+    out = []
+    with open(os.path.join(GOLDEN, "toy_tasks_p3.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                out.append(tuple(int(x) for x in line.split()))
+    return out
+
+
+def positions_by_definition(n, rowptr, colidx):
+    """(rank, perm, oriented out-degree) from the dense adjacency and Sec. 4.1's rule."""
+    A = G.dense_adjacency(n, rowptr, colidx)
+    deg = A.sum(axis=1)
+    perm = np.lexsort((np.arange(n), deg))      # by degree, then id
+    rank = np.empty(n, dtype=np.int64)
+    rank[perm] = np.arange(n)
+    ar, br = np.nonzero(np.triu(A, 1))
+    lo = np.minimum(rank[ar], rank[br])
+    outdeg = np.bincount(lo, minlength=n)
+    return A, deg, rank, perm, outdeg
+
+
+def cuts_by_definition(n, outdeg_by_position, p):
+    rp = np.concatenate([[0], np.cumsum(outdeg_by_position)])
+    m = int(rp[-1])
+    c = [0]
+    for i in range(1, p):
+        target = -(-i * m // p)
+        r = 0
+        while r < n and rp[r] < target:
+            r += 1
+        c.append(r)
+    c.append(n)
+    return np.array(c, dtype=np.int64)
+
+
+def per_task_brute(n, rowptr, colidx, p):
+    """Per-task counts by enumerating vertex triples and placing each triangle."""
+    A, deg, rank, perm, outdeg = positions_by_definition(n, rowptr, colidx)
+    c = cuts_by_definition(n, outdeg[np.arange(n)], p)
+    part = np.searchsorted(c, np.arange(n), side="right") - 1
+    part = np.minimum(part, p - 1)
+    index = {}
+    for i in range(p):
+        for j in range(i, p):
+            for k in range(j, p):
+                index[(i, j, k)] = len(index)
+    out = np.zeros(len(index), dtype=np.uint64)
+    for a in range(n):
+        for b in range(a + 1, n):
+            if not A[a, b]:
+                continue
+            for d in range(b + 1, n):
+                if A[a, d] and A[b, d]:
+                    x, y, z = sorted((rank[a], rank[b], rank[d]))
+                    out[index[(int(part[x]), int(part[y]), int(part[z]))]] += 1
+    return out
+
+
+def with_noise(n, rowptr, colidx, rng, dup=0.3, loops=3):
+    """Same simple graph, with duplicate entries and self-loops added."""
+    rows = [list(colidx[rowptr[v]:rowptr[v + 1]]) for v in range(n)]
+    for v in range(n):
+        extra = [x for x in rows[v] if rng.random() < dup]
+        rows[v] += extra
+    for _ in range(loops):
+        if n:
+            v = int(rng.integers(0, n))
+            rows[v].append(v)
+    for v in range(n):
+        rng.shuffle(rows[v])
+    rp = np.zeros(n + 1, dtype=np.int64)
+    for v in range(n):
+        rp[v + 1] = rp[v] + len(rows[v])
+    ci = np.array([x for r in rows for x in r], dtype=np.int32)
+    return n, rp, ci
+
+
+def pin_battery() -> list[str]:
+    fails: list[str] = []
+
+    def check(cond, msg):
+        if not cond:
+            fails.append(msg)
+
+    rng = np.random.default_rng(12345)
+
+    # Alg. 1 against set intersection on random sorted lists
+    for _ in range(200):
+        A = np.unique(rng.integers(0, 40, rng.integers(0, 20)))
+        B = np.unique(rng.integers(0, 40, rng.integers(0, 20)))
+        check(oracle.n_intersect(A, B) == len(set(A.tolist()) & set(B.tolist())),
+              f"Alg.1 on {A.tolist()} {B.tolist()}")
+        if fails:
+            break
+
+    # task composition: Tab. 4 pairs and the toy example
+    for tiles, tasks in load_table4_pairs():
+        p = int(round(tiles ** 0.5))
+        check(p * p == tiles and oracle.num_tasks(p) == tasks, f"|T| for tiles={tiles}")
+        check(oracle.task_list(p).shape[0] == tasks, f"Alg.4 length for p={p}")
+    check([tuple(t) for t in oracle.task_list(3).tolist()] == load_toy_tasks(), "toy task list")
+
+    # closed forms
+    for k in (3, 5, 8):
+        r = oracle.bbtc(*G.complete(k), p=2, want_per_vertex=True)
+        check(r["total"] == G.choose(k, 3), f"K_{k}")
+        check(np.all(r["per_vertex"] == G.choose(k - 1, 2)), f"K_{k} per-vertex")
+    for k in (4, 7):
+        r = oracle.bbtc(*G.wheel(k), p=3, method="hmap", want_per_vertex=True)
+        pv = r["per_vertex"]
+        check(r["total"] == k and pv[0] == k and np.all(pv[1:] == 2), f"wheel W_{k}")
+    r = oracle.bbtc(*G.complete_multipartite([2, 3, 4]), p=3)
+    check(r["total"] == 24, "K_{2,3,4}")
+    check(oracle.bbtc(*G.grid(4, 5), p=2)["total"] == 0, "grid")
+
+    # random graphs with noise: brute force, trace(A^3)/6, per-vertex, per task
+    for trial in range(12):
+        n = int(rng.integers(6, 22))
+        g = G.gnp(n, float(rng.uniform(0.2, 0.8)), rng)
+        noisy = with_noise(*g, rng)
+        T = G.brute_force_triangles(*g)
+        check(G.trace_cubed_over_six(*g) == T, "brute vs trace (test helper)")
+        pr = oracle.prepare(*noisy)
+        check(pr["m"] == int(G.dense_adjacency(*g).sum() // 2), f"canonical edge count trial {trial}")
+        check(oracle.tc_intersect(n, pr["rowptr"], pr["colidx"]) == T, f"Alg.2 trial {trial}")
+        check(oracle.tc_hmap(n, pr["rowptr"], pr["colidx"]) == T, f"Alg.3 trial {trial}")
+        pv = oracle.per_vertex(n, pr["rowptr"], pr["colidx"], pr["perm"])
+        check(np.array_equal(pv, G.per_vertex_dense(*g)), f"per-vertex trial {trial}")
+        # the order: degree non-decreasing along positions, ties by id, edges upward
+        A, deg, rank, perm, outdeg = positions_by_definition(*g)
+        check(np.array_equal(pr["perm"], perm), f"degree order trial {trial}")
+        check(np.array_equal(np.diff(pr["rowptr"]), outdeg), f"out-degrees trial {trial}")
+        for p in (1, 2, 3, 5):
+            c = oracle.cuts(n, pr["rowptr"], p)
+            check(np.array_equal(c, cuts_by_definition(n, outdeg, p)), f"cuts p={p} trial {trial}")
+            brute = per_task_brute(*g, p)
+            r5 = oracle.bbtc(*noisy, p=p, method="intersect", prep=pr)
+            r6 = oracle.bbtc(*noisy, p=p, method="hmap", prep=pr)
+            cls = oracle.classify_triangles(n, pr["rowptr"], pr["colidx"], p, c)
+            check(np.array_equal(r5["per_task"], brute), f"Alg.5 per task p={p} trial {trial}")
+            check(np.array_equal(r6["per_task"], brute), f"Alg.6 per task p={p} trial {trial}")
+            check(np.array_equal(cls, brute), f"classified per task p={p} trial {trial}")
+        if len(fails) > 20:
+            break
+
+    # ExecTime on a hand-worked example: p=2, cuts [0,2,5],
+    # |G_00|=3, |G_01|=4, |G_11|=6 -> delta(G_00)=1.5, delta(G_01)=2, delta(G_11)=2
+    # tasks (0,0,0): 3*1.5=4.5 ; (0,0,1): 3*max(2,2)=6 ; (0,1,1): 4*max(2,2)=8 ;
+    # (1,1,1): 6*2=12
+    est = oracle.exec_time(2, np.array([0, 2, 5]), np.array([[3, 4], [0, 6]]))
+    check(np.allclose(est, [4.5, 6.0, 8.0, 12.0]), f"ExecTime example {est.tolist()}")
+    # p=2, cuts [0,4,5], |G_00|=2, |G_01|=1, |G_11|=3: delta = 0.5, 0.25, 3
+    # -> (0,0,0)=2*0.5, (0,0,1)=2*0.25, (0,1,1)=1*max(0.25,3), (1,1,1)=3*3
+    est = oracle.exec_time(2, np.array([0, 4, 5]), np.array([[2, 1], [0, 3]]))
+    check(np.allclose(est, [2 * 0.5, 2 * 0.25, 1 * 3.0, 3 * 3.0]), f"ExecTime example 2 {est.tolist()}")
+    order = oracle.order_tasks(np.array([1.0, 3.0, 3.0, 2.0]))
+    check(order.tolist() == [1, 2, 3, 0], "task order: non-increasing, ties in Alg.4 order")
+
+    # algorithmic-bytes figures on a path a-b-c plus triangle: by hand
+    n, rp, ci = G.csr_from_edges(4, [(0, 1), (1, 2), (0, 2), (2, 3)])
+    pr = oracle.prepare(n, rp, ci)
+    wf = oracle.work_figures(n, pr["rowptr"], pr["colidx"])
+    d = np.diff(pr["rowptr"])
+    wedges = sum(int(d[v]) for u in range(n) for v in pr["colidx"][pr["rowptr"][u]:pr["rowptr"][u + 1]])
+    check(wf["wedges"] == wedges and wf["wmin"] == 4 * (4 + wedges), "work figures")
+    return fails
