@@ -1,0 +1,353 @@
+"""Benchmark of block-based triangle counting on one GB300 (or N replicas).
+
+One step = the whole path on one synthetic graph already resident in device
+memory: canonical edge set, degree order and orientation (bbtc_graph_create),
+then partition, blocks, tasks, estimate/order and the per-task counting
+kernel with the reduction (bbtc_count), then bbtc_graph_destroy.
+
+Metric: oriented edges counted per second (m / step time; m = simple
+undirected edges = oriented edges), whole job over all ranks. `e2e` repeats
+the step through the same public calls from pinned HOST buffers, so the
+host-to-device copy of the input CSR and the device-to-host read of the count
+are inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload rmat-s23|rmat-s14|chunglu-friendster] [--p P]
+                       [--kernel auto|intersect|hashmap]
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the graph's tasks need no exchange); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "oriented edges/s counted (excl./incl. H2D), % HBM roofline; p50/p99 req latency"
+UNIT = "edges/s"
+
+WORKLOADS = {
+    # name: (description, generator call)
+    "rmat-s23": "R-MAT scale 23 (8,388,608 vertices), edge factor 16, a/b/c/d = "
+                ".57/.19/.19/.05, seed 2; symmetrised, self-loops and duplicates removed "
+                "by the path itself",
+    "rmat-s14": "R-MAT scale 14 (16,384 vertices), edge factor 16, a/b/c/d = "
+                ".57/.19/.19/.05, seed 1",
+    "chunglu-friendster": "Friendster-shaped Chung-Lu: 65,608,366 vertices, 1,806,067,135 "
+                          "pairs, degree exponent 2.1, expected degree capped at 5,000, seed 3",
+}
+DEFAULT_P = {"rmat-s23": 4, "rmat-s14": 2, "chunglu-friendster": 8}
+
+
+def make_graph(name: str):
+    import graphgen
+    if name == "rmat-s23":
+        return graphgen.rmat_s23()
+    if name == "rmat-s14":
+        return graphgen.rmat_s14()
+    if name == "chunglu-friendster":
+        return graphgen.chunglu_friendster()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_sample_scale(steps_total: int, budget_s: float = 150.0) -> int:
+    """Largest R-MAT scale (same recipe) whose oracle pass fits budget_s / steps."""
+    per_step = budget_s / max(steps_total, 1)
+    scale = 12
+    for s in range(12, 20):
+        if 8.0 * 2.3 ** (s - 18) <= per_step:  # measured: ~6-8 s at scale 18
+            scale = s
+    return scale
+
+
+def run_oracle_sample(scale: int, p: int):
+    """Oracle pipeline (prepare + Alg. 5 per task) on R-MAT `scale`, ef 16, seed 2."""
+    import graphgen
+    import oracle
+    n, rp, ci = graphgen.rmat(scale, 16, 2)
+    t0 = time.perf_counter()
+    r = oracle.bbtc(n, rp, ci, p=p)
+    dt = time.perf_counter() - t0
+    return r["m"], dt, r["total"]
+
+
+def cpu_baseline(steps_total: int, p: int):
+    scale = oracle_sample_scale(steps_total, budget_s=30.0 * steps_total)
+    scale = min(scale, 19)
+    m, dt, total = run_oracle_sample(scale, p)
+    return {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle pipeline (canonicalise, order, orient, partition p={p}, "
+                      f"Alg. 5 per task) on R-MAT scale {scale}, edge factor 16, seed 2 "
+                      f"({m} edges, {dt:.2f} s, {total} triangles); single-threaded C"}
+
+
+def reference_arm(args, rank: int, world: int):
+    if rank != 0:
+        return
+    steps_total = args.steps + args.warmup
+    scale = oracle_sample_scale(steps_total)
+    p = args.p or DEFAULT_P.get(args.workload, 4)
+    for _ in range(args.warmup):
+        run_oracle_sample(scale, p)
+    times, m = [], 0
+    for _ in range(args.steps):
+        m, dt, _ = run_oracle_sample(scale, p)
+        times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    value = m / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "p": p,
+                   "sample": f"R-MAT scale {scale}, edge factor 16, seed 2 ({m} edges)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"R-MAT scale {scale}, edge factor 16, seed 2 per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU path
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat-s23", choices=sorted(WORKLOADS))
+    ap.add_argument("--p", type=int, default=0)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "intersect", "hashmap"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import paper_2009_12457_gb300 as bb
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    p = args.p or DEFAULT_P.get(args.workload, 4)
+    n, rp, ci = make_graph(args.workload)
+    flags = bb.INPUT_SYMMETRIC  # the generator lists every pair under both endpoints
+    stream = torch.cuda.Stream()
+    h_rp = torch.from_numpy(rp).pin_memory()
+    h_ci = torch.from_numpy(ci).pin_memory()
+    d_rp = h_rp.cuda()
+    d_ci = h_ci.cuda()
+    torch.cuda.synchronize()
+    del rp, ci
+
+    def step(device_resident: bool):
+        if device_resident:
+            h = bb.bbtc_graph_create_async(n, d_rp, d_ci, flags, stream)
+        else:
+            h = bb.bbtc_graph_create_async(n, h_rp, h_ci, flags, stream)
+        try:
+            total = bb.bbtc_count(h, bb.make_opts(p=p, kernel=args.kernel, stream=stream))
+            info = bb.bbtc_graph_get_info(h) if device_resident else None
+            tim = bb.bbtc_graph_get_timings(h) if device_resident else None
+        finally:
+            bb.bbtc_graph_destroy(h)
+        return total, info, tim
+
+    # warm-up (also validates that every step gives the same count)
+    totals = set()
+    info = None
+    for _ in range(args.warmup):
+        total, info, _ = step(True)
+        totals.add(total)
+    m = info["m"]
+
+    # timed: device-resident inputs
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    count_ms, prep_ms, plan_ms = [], [], []
+    launches0 = bb.bbtc_kernel_launches()
+    with ClockSampler(local_rank) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            total, _, tim = step(True)
+            totals.add(total)
+            count_ms.append(tim["count_ms"])
+            prep_ms.append(tim["prep_ms"])
+            plan_ms.append(tim["plan_ms"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = bb.bbtc_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # timed: host inputs through the same calls (H2D and count D2H inside)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        total, _, _ = step(False)
+        totals.add(total)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    barrier()
+
+    if len(totals) != 1:
+        raise SystemExit(f"inconsistent triangle counts across steps: {sorted(totals)}")
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        kms = sum(count_ms) / len(count_ms)
+        wmin = 4 * (m + info["wedges_in"])
+        achieved = wmin / (kms / 1000.0) / 1e9
+        h2d = (n + 1) * 8 + int(h_ci.numel()) * 4
+        line = {
+            "metric": METRIC,
+            "value": world * m / (ms / 1000.0),
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "int32",
+            "data": "synthetic",
+            "config": {
+                "workload": WORKLOADS[args.workload], "p": p, "kernel": args.kernel,
+                "n": n, "m": m, "triangles": next(iter(totals)),
+                "input_entries": int(h_ci.numel()),
+                "l2": "inputs larger than L2 (input CSR %.2f GB, oriented CSR %.2f GB)"
+                      % (h2d / 1e9, (m * 8 + (n + 1) * 8) / 1e9),
+                "parallelism": "replicas" if world > 1 else "single GPU",
+                "phase_ms": {"prep": statistics.mean(prep_ms), "plan": statistics.mean(plan_ms),
+                             "count_kernel": kms},
+            },
+            "e2e": {"value": world * m / (e2e_ms / 1000.0), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_count (per-task counting, a9)",
+                         "algorithmic_bytes": wmin,
+                         "bytes_formula": "4*(m + sum over oriented edges (u,v) of d+(v))",
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "clocks": clocks.summary(),
+            "gpu_launches": launches,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(1, p)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * bbtc.h -- C ABI of the block-based triangle counting library (sm_103a).
+ *
+ * Method: Yasar, Rajamanickam, Berry & Catalyurek, "A Block-Based Triangle
+ * Counting Algorithm on Heterogeneous Environments" (arXiv 2009.12457).
+ *
+ * The library counts the 3-cliques of a simple undirected graph (Sec. 2,
+ * "Triangle Counting Problem") with the paper's pipeline, every step of which
+ * runs in this library's own CUDA kernels on one GPU:
+ *
+ *   bbtc_graph_create : canonical simple edge set, degree, non-decreasing
+ *                       degree order, orientation u < v (Sec. 2, Sec. 4.1)
+ *   bbtc_count        : p x p symmetric partition and blocks G_ij (Sec. 2,
+ *                       Sec. 4.1), task composition (Sec. 4.2, Alg. 4), task
+ *                       estimate and order (Sec. 5), per-task counting by
+ *                       bbTC-Intersect (Alg. 5) or bbTC-HMap (Alg. 6), and the
+ *                       sum of the per-task counts (Alg. 9).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a bbtc_status; no call aborts or traps. On an error,
+ *    outputs are left untouched and bbtc_last_error() describes the cause.
+ *  - Ids are int32 (n <= 2^31 - 1), edge offsets int64, counts uint64.
+ *  - Pointers are HOST pointers unless a flag or field says otherwise.
+ *  - A handle is not thread-safe; distinct handles may be used from distinct
+ *    host threads.
+ *  - Calls are synchronous with respect to the host: when a call returns, its
+ *    outputs are written and the caller's input buffers are no longer read.
+ */
+#ifndef BBTC_H
+#define BBTC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bbtc_graph *bbtc_graph_t; /* opaque; owns the device-resident oriented CSR */
+
+typedef enum {
+  BBTC_OK = 0,
+  BBTC_EINVAL = 1,     /* invalid argument or malformed CSR */
+  BBTC_ENOMEM = 2,     /* device or host allocation failed, or the budget is too small */
+  BBTC_ECUDA = 3,      /* a CUDA runtime call failed */
+  BBTC_ETIMEOUT = 4,   /* a bounded device wait ran out (opts.timeout_ms) */
+  BBTC_ECANCELLED = 5, /* the request was cancelled before it ran */
+  BBTC_EINTERNAL = 6   /* an internal consistency check failed */
+} bbtc_status;
+
+/* Per-task counting kernel (Sec. 4.3; the paper's isDense choice, Alg. 7). */
+typedef enum {
+  BBTC_KERNEL_AUTO = 0,      /* choose per task from the block densities */
+  BBTC_KERNEL_INTERSECT = 1, /* bbTC-Intersect (Alg. 5): sorted-list search */
+  BBTC_KERNEL_HASHMAP = 2    /* bbTC-HMap (Alg. 6): hash-table lookup */
+} bbtc_kernel;
+
+/* bbtc_graph_create flags */
+#define BBTC_INPUT_DEVICE 0x1u    /* rowptr/colidx are DEVICE pointers on the current device */
+#define BBTC_INPUT_SYMMETRIC 0x2u /* caller guarantees every edge is listed under both
+                                     endpoints; only entries u < v are then read as edges */
+
+typedef struct {
+  uint32_t struct_size;         /* sizeof(bbtc_opts); set by bbtc_opts_init */
+  int32_t p;                    /* blocks per side, 1 <= p <= 64; 0 = choose from the graph */
+  int32_t kernel;               /* bbtc_kernel */
+  uint32_t timeout_ms;          /* 0 = no limit on the counting kernel's bounded waits */
+  uint64_t device_budget_bytes; /* 0 = graph resident; else blocks stream under this budget */
+  uint64_t *per_vertex_out;     /* NULL, or n uint64 (ORIGINAL ids): triangles at each vertex */
+  uint64_t *per_task_out;       /* NULL, or bbtc_num_tasks(p) uint64 in Alg. 4 order */
+  void *stream;                 /* cudaStream_t to run on; NULL = the handle's own stream */
+  uint32_t flags;               /* BBTC_OUT_DEVICE: the two output arrays are device pointers */
+  int32_t hash_threshold;       /* AUTO: tasks whose mean staged list exceeds this use HMap;
+                                   0 = built-in default */
+} bbtc_opts;
+
+#define BBTC_OUT_DEVICE 0x1u
+
+/* Fill *opts with defaults (p = 0, AUTO kernel, resident, no optional outputs). */
+void bbtc_opts_init(bbtc_opts *opts);
+
+/*
+ * Copy an undirected graph into a new handle and run the graph-only steps of
+ * the method: drop self-loops and duplicate entries (Sec. 2 assumes a simple
+ * graph), compute degrees, order vertices by (degree, id) ascending (Sec. 4.1;
+ * ties by original id), and orient every edge from the lower to the higher
+ * position (Sec. 2: N(G,u) = {v : (u,v) in E, u < v}).
+ *
+ *   n       number of vertices, 0 <= n <= 2^31 - 1
+ *   rowptr  n+1 int64 offsets, rowptr[0] = 0, non-decreasing
+ *   colidx  rowptr[n] int32 neighbour ids in [0, n); an edge may be listed
+ *           under one or both endpoints, in any order, repeated, and
+ *           self-loops are allowed (all are ignored beyond the simple graph)
+ *   flags   BBTC_INPUT_DEVICE and/or BBTC_INPUT_SYMMETRIC
+ *   out     receives the handle
+ *
+ * Ownership: the caller keeps rowptr/colidx (they are only read during the
+ * call). The handle owns its device memory until bbtc_graph_destroy.
+ * Errors: EINVAL for n out of range, NULL pointers with edges present,
+ * rowptr[0] != 0, a decreasing rowptr, or any colidx outside [0, n), or more
+ * than 2^32 - 1 simple edges; ENOMEM; ECUDA.
+ */
+bbtc_status bbtc_graph_create(int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                              uint32_t flags, bbtc_graph_t *out);
+
+/* As bbtc_graph_create, but run on `stream` (a cudaStream_t; NULL = a new
+ * stream owned by the handle). The handle keeps using `stream` by default. */
+bbtc_status bbtc_graph_create_async(int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                                    uint32_t flags, void *stream, bbtc_graph_t *out);
+
+/*
+ * Count the triangles of the handle's graph with bbTC at p x p blocks:
+ * contiguous symmetric partition of the degree order balanced on oriented
+ * edges, tasks (i,j,k), i <= j <= k (Alg. 4), ordered by the Sec. 5 estimate
+ * and drained by a persistent work-stealing kernel, each task counted as
+ * sum over (u,v) in G_ij of |N(G_ik,u) ∩ N(G_jk,v)| (Alg. 5 / Alg. 6).
+ *
+ *   count  receives the exact total (host uint64)
+ *   opts   NULL = defaults; see bbtc_opts for the optional outputs
+ *
+ * Errors: EINVAL (p outside 0..64, opts->struct_size too small), ENOMEM
+ * (also when device_budget_bytes cannot hold one task's blocks), ETIMEOUT,
+ * ECUDA.
+ */
+bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts, uint64_t *count);
+
+/*
+ * Count ng independent graphs in one persistent launch. counts receives ng
+ * uint64 totals; per_graph (nullable) receives each graph's status. Options
+ * other than p, kernel and stream apply to none of the graphs (per-task and
+ * per-vertex outputs are not produced in batch mode). p = 0 picks p per graph.
+ * Errors: EINVAL for ng < 0 or a NULL handle; the first failing graph's status.
+ */
+bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts *opts,
+                             uint64_t *counts, bbtc_status *per_graph);
+
+/* Free the handle and its device memory. Accepts NULL. */
+void bbtc_graph_destroy(bbtc_graph_t g);
+
+/* Message of the calling thread's most recent error ("" if none). */
+const char *bbtc_last_error(void);
+
+/* Number of tasks for p parts: p(p+1)(p+2)/6 (Sec. 4.2). 0 for p < 1. */
+uint64_t bbtc_num_tasks(int32_t p);
+
+/* ------------------------------------------------------------ inspection */
+
+typedef struct {
+  int64_t n;             /* vertices */
+  int64_t m;             /* simple undirected edges (= oriented edges) */
+  int64_t dplus_max;     /* largest out-degree after orientation */
+  int64_t deg_max;       /* largest undirected degree */
+  uint64_t device_bytes; /* device memory held by the handle */
+  uint64_t wedges_in;    /* sum over oriented edges (u,v) of d+(v) */
+  uint64_t wedges_out;   /* sum over vertices u of d+(u)(d+(u)-1)/2 */
+} bbtc_graph_info;
+
+/* Sizes and work figures of the handle's graph (the two wedge sums are
+ * computed on the device at the first call). */
+bbtc_status bbtc_graph_get_info(bbtc_graph_t g, bbtc_graph_info *info);
+
+/* Device time of the handle's most recent steps, measured with CUDA events
+ * on the stream each step ran on. */
+typedef struct {
+  double prep_ms;      /* bbtc_graph_create: a1-a4 (after any host-to-device copy) */
+  double plan_ms;      /* last bbtc_count: a5-a8 (0 when the plan was reused) */
+  double count_ms;     /* last bbtc_count: the counting kernel (a9) */
+  int64_t work_items;  /* work items drained by that kernel */
+} bbtc_timings;
+
+bbtc_status bbtc_graph_get_timings(bbtc_graph_t g, bbtc_timings *t);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t bbtc_kernel_launches(void);
+
+/*
+ * Copy the oriented CSR to host arrays (any may be NULL to skip it):
+ * rowptr n+1 int64 and colidx m int32 in degree-order positions (rows sorted
+ * ascending), perm n int32 (perm[r] = original id at position r), degree n
+ * int64 (undirected simple degree by ORIGINAL id).
+ */
+bbtc_status bbtc_graph_get_oriented(bbtc_graph_t g, int64_t *rowptr, int32_t *colidx,
+                                    int32_t *perm, int64_t *degree);
+
+/*
+ * The plan bbtc_count builds for p (Sec. 2, Sec. 4.2, Sec. 5), as host copies
+ * (any output may be NULL): cuts p+1 int32 (c_0 = 0, c_p = n), block_nnz p*p
+ * int64 (|G_ij|, row-major), tasks 3*|T| int32 ((i,j,k) in Alg. 4 order),
+ * estimate |T| double (ExecTime in Alg. 4 order), order |T| int32 (task
+ * indices, non-increasing estimate, ties in Alg. 4 order).
+ */
+bbtc_status bbtc_graph_get_plan(bbtc_graph_t g, int32_t p, int32_t *cuts, int64_t *block_nnz,
+                                int32_t *tasks, double *estimate, int32_t *order);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBTC_H */

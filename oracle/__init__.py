@@ -100,6 +100,8 @@ def _declare(lib):
     lib.orc_bbtc_hmap_task.restype = u64
     lib.orc_classify_triangles.argtypes = [i64, P, P, i32, P, P]
     lib.orc_work_figures.argtypes = [i64, P, P, P, P, P]
+    lib.orc_vertex_triangles.argtypes = [i64, P, P, i64]
+    lib.orc_vertex_triangles.restype = u64
     return lib
 
 
@@ -238,6 +240,12 @@ def work_figures(n: int, rp, ci) -> dict:
     a = np.zeros(3, dtype=np.uint64)
     _load().orc_work_figures(n, _p(rp), _p(ci), _p(a[0:]), _p(a[1:]), _p(a[2:]))
     return {"wmin": int(a[0]), "wmerge": int(a[1]), "wedges": int(a[2])}
+
+
+def vertex_triangles(n: int, rowptr, colidx, x: int) -> int:
+    """Triangles containing original vertex x, from a symmetric input CSR."""
+    rowptr, colidx = _c(rowptr, np.int64), _c(colidx, np.int32)
+    return int(_load().orc_vertex_triangles(n, _p(rowptr), _p(colidx), x))
 
 
 # ---------------------------------------------------------- full pipeline

@@ -393,3 +393,49 @@ void orc_work_figures(int64_t n, const int64_t *rp, const int32_t *ci, uint64_t 
   *wmerge = 4 * mg;
   *wedges = w;
 }
+
+/* ------------------------------------------- single-vertex count (sampling) */
+
+static int cmp_i32(const void *x, const void *y) {
+  int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+  return (a > b) - (a < b);
+}
+
+/* sorted distinct neighbours of x other than x itself; returns their number */
+static int64_t simple_neighbours(const int64_t *rowptr, const int32_t *colidx, int64_t x,
+                                 int32_t *buf) {
+  int64_t len = 0;
+  for (int64_t e = rowptr[x]; e < rowptr[x + 1]; ++e)
+    if (colidx[e] != x) buf[len++] = colidx[e];
+  qsort(buf, (size_t)len, sizeof(int32_t), cmp_i32);
+  int64_t u = 0;
+  for (int64_t i = 0; i < len; ++i)
+    if (i == 0 || buf[i] != buf[i - 1]) buf[u++] = buf[i];
+  return u;
+}
+
+/*
+ * Triangles containing vertex x, by the definition (Sec. 2): the number of
+ * edges {y, z} between two distinct neighbours y < z of x. Reads the input
+ * CSR directly, which must list every edge under both endpoints. Used to
+ * check sampled per-vertex counts on graphs too large for the full oracle.
+ */
+uint64_t orc_vertex_triangles(int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                              int64_t x) {
+  (void)n;
+  int64_t dx = rowptr[x + 1] - rowptr[x];
+  int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)(dx > 0 ? dx : 1));
+  int64_t ns = simple_neighbours(rowptr, colidx, x, S);
+  uint64_t t = 0;
+  for (int64_t a = 0; a < ns; ++a) {
+    int64_t y = S[a];
+    int64_t dy = rowptr[y + 1] - rowptr[y];
+    int32_t *Ny = (int32_t *)malloc(sizeof(int32_t) * (size_t)(dy > 0 ? dy : 1));
+    int64_t ny = simple_neighbours(rowptr, colidx, y, Ny);
+    /* common elements of S and Ny that are greater than y */
+    t += orc_n_intersect(S + a + 1, ns - a - 1, Ny, ny);
+    free(Ny);
+  }
+  free(S);
+  return t;
+}

@@ -1,0 +1,510 @@
+// api.cu -- the extern "C" entry points declared in include/bbtc.h.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stddef.h>
+#include <string.h>
+
+#include <new>
+
+#include "graph.cuh"
+#include "primitives.cuh"
+
+namespace bbtc {
+
+namespace {
+thread_local char g_error[1024] = "";
+bool g_pool_ready[64] = {false};
+unsigned long long g_launches = 0;
+}  // namespace
+
+void note_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+
+bbtc_status launch_status(const char *where) {
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("%s: kernel launch failed: %s", where, cudaGetErrorString(e));
+    return BBTC_ECUDA;
+  }
+  return BBTC_OK;
+}
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_error, sizeof(g_error), fmt, ap);
+  va_end(ap);
+}
+
+void clear_error() { g_error[0] = '\0'; }
+
+bbtc_status dalloc(void **p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_error("cudaGetDevice failed");
+    return BBTC_ECUDA;
+  }
+  if (dev >= 0 && dev < 64 && !g_pool_ready[dev]) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t threshold = ~0ull;  // keep freed blocks cached for the next call
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+    }
+    g_pool_ready[dev] = true;
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BBTC_ENOMEM : BBTC_ECUDA;
+  }
+  return BBTC_OK;
+}
+
+void dfree(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+}  // namespace bbtc
+
+namespace bbtc {
+namespace {
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void destroy_graph(bbtc_graph *g) {
+  if (!g) return;
+  cudaStream_t s = g->stream;
+  free_plan(&g->plan, s);
+  dfree(g->rowptr, s);
+  dfree(g->colidx, s);
+  dfree(g->esrc, s);
+  dfree(g->perm, s);
+  dfree(g->deg, s);
+  cudaStreamSynchronize(s);
+  for (cudaEvent_t &e : g->ev)
+    if (e) cudaEventDestroy(e);
+  if (g->own_stream) cudaStreamDestroy(s);
+  delete g;
+}
+
+__global__ void k_scatter_by_perm(const unsigned long long *__restrict__ by_pos,
+                                  const int32_t *__restrict__ perm, int64_t n,
+                                  unsigned long long *__restrict__ by_id) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x)
+    by_id[perm[r]] = by_pos[r];
+}
+
+bbtc_status check_opts(const bbtc_opts *opts, bbtc_opts *out) {
+  bbtc_opts_init(out);
+  if (opts) {
+    if (opts->struct_size < sizeof(bbtc_opts)) {
+      set_error("bbtc_opts.struct_size is %u, expected %zu (call bbtc_opts_init)",
+                opts->struct_size, sizeof(bbtc_opts));
+      return BBTC_EINVAL;
+    }
+    *out = *opts;
+  }
+  if (out->p < 0 || out->p > 64) {
+    set_error("p = %d is outside 0..64", out->p);
+    return BBTC_EINVAL;
+  }
+  if (out->kernel < BBTC_KERNEL_AUTO || out->kernel > BBTC_KERNEL_HASHMAP) {
+    set_error("kernel = %d is not a bbtc_kernel", out->kernel);
+    return BBTC_EINVAL;
+  }
+  if (out->hash_threshold < 0) {
+    set_error("hash_threshold = %d is negative", out->hash_threshold);
+    return BBTC_EINVAL;
+  }
+  if (out->hash_threshold == 0) out->hash_threshold = 16;
+  return BBTC_OK;
+}
+
+}  // namespace
+}  // namespace bbtc
+
+using namespace bbtc;
+
+extern "C" {
+
+void bbtc_opts_init(bbtc_opts *opts) {
+  if (!opts) return;
+  memset(opts, 0, sizeof(*opts));
+  opts->struct_size = sizeof(bbtc_opts);
+  opts->kernel = BBTC_KERNEL_AUTO;
+}
+
+const char *bbtc_last_error(void) { return g_error; }
+
+uint64_t bbtc_num_tasks(int32_t p) {
+  if (p < 1) return 0;
+  return (uint64_t)p * (uint64_t)(p + 1) * (uint64_t)(p + 2) / 6;
+}
+
+bbtc_status bbtc_graph_create_async(int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                                    uint32_t flags, void *stream, bbtc_graph_t *out) {
+  clear_error();
+  if (!out) {
+    set_error("bbtc_graph_create: out is NULL");
+    return BBTC_EINVAL;
+  }
+  if (n < 0 || n > 0x7fffffffLL) {
+    set_error("bbtc_graph_create: n = %lld is outside [0, 2^31 - 1]", (long long)n);
+    return BBTC_EINVAL;
+  }
+  if (flags & ~(BBTC_INPUT_DEVICE | BBTC_INPUT_SYMMETRIC)) {
+    set_error("bbtc_graph_create: unknown flags 0x%x", flags);
+    return BBTC_EINVAL;
+  }
+  if (!rowptr) {
+    set_error("bbtc_graph_create: rowptr is NULL");
+    return BBTC_EINVAL;
+  }
+  const bool on_device = (flags & BBTC_INPUT_DEVICE) != 0;
+  bbtc_graph *g = new (std::nothrow) bbtc_graph();
+  if (!g) {
+    set_error("bbtc_graph_create: host allocation failed");
+    return BBTC_ENOMEM;
+  }
+  cudaGetDevice(&g->device);
+  g->n = n;
+  if (stream) {
+    g->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      set_error("bbtc_graph_create: cudaStreamCreate failed");
+      delete g;
+      return BBTC_ECUDA;
+    }
+    g->own_stream = true;
+  }
+  cudaStream_t s = g->stream;
+  for (cudaEvent_t &e : g->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      set_error("bbtc_graph_create: cudaEventCreate failed");
+      destroy_graph(g);
+      return BBTC_ECUDA;
+    }
+  }
+  bbtc_status st = BBTC_OK;
+  int64_t nnz = 0;
+  int64_t *d_rowptr = nullptr;
+  int32_t *d_colidx = nullptr;
+  bool copied = false;
+  do {
+    if (on_device) {
+      if (cudaMemcpyAsync(&nnz, rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("bbtc_graph_create: reading rowptr[n] from the device failed");
+        st = BBTC_ECUDA;
+        break;
+      }
+    } else {
+      nnz = rowptr[n];
+    }
+    if (nnz < 0) {
+      set_error("bbtc_graph_create: rowptr[n] = %lld is negative", (long long)nnz);
+      st = BBTC_EINVAL;
+      break;
+    }
+    if (nnz > 0 && !colidx) {
+      set_error("bbtc_graph_create: colidx is NULL with %lld entries", (long long)nnz);
+      st = BBTC_EINVAL;
+      break;
+    }
+    if (on_device) {
+      d_rowptr = const_cast<int64_t *>(rowptr);
+      d_colidx = const_cast<int32_t *>(colidx);
+    } else {
+      copied = true;
+      if ((st = dalloc_n(&d_rowptr, n + 1, s)) != BBTC_OK) break;
+      if ((st = dalloc_n(&d_colidx, nnz, s)) != BBTC_OK) break;
+      if (cudaMemcpyAsync(d_rowptr, rowptr, sizeof(int64_t) * (size_t)(n + 1),
+                          cudaMemcpyHostToDevice, s) != cudaSuccess ||
+          (nnz > 0 && cudaMemcpyAsync(d_colidx, colidx, sizeof(int32_t) * (size_t)nnz,
+                                      cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+        set_error("bbtc_graph_create: host-to-device copy failed");
+        st = BBTC_ECUDA;
+        break;
+      }
+    }
+    if (cudaEventRecord(g->ev[0], s) != cudaSuccess) {
+      set_error("bbtc_graph_create: cudaEventRecord failed");
+      st = BBTC_ECUDA;
+      break;
+    }
+    st = prepare_graph(g, d_rowptr, d_colidx, nnz, (flags & BBTC_INPUT_SYMMETRIC) != 0);
+    if (st == BBTC_OK && cudaEventRecord(g->ev[1], s) != cudaSuccess) {
+      set_error("bbtc_graph_create: cudaEventRecord failed");
+      st = BBTC_ECUDA;
+    }
+  } while (0);
+  if (copied) {
+    dfree(d_rowptr, s);
+    dfree(d_colidx, s);
+  }
+  if (st == BBTC_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("bbtc_graph_create: %s", cudaGetErrorString(cudaGetLastError()));
+    st = BBTC_ECUDA;
+  }
+  if (st != BBTC_OK) {
+    destroy_graph(g);
+    return st;
+  }
+  *out = g;
+  return BBTC_OK;
+}
+
+bbtc_status bbtc_graph_create(int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                              uint32_t flags, bbtc_graph_t *out) {
+  return bbtc_graph_create_async(n, rowptr, colidx, flags, nullptr, out);
+}
+
+void bbtc_graph_destroy(bbtc_graph_t g) {
+  if (!g) return;
+  DeviceGuard dg(g->device);
+  destroy_graph(g);
+}
+
+bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count) {
+  clear_error();
+  if (!g || !count) {
+    set_error("bbtc_count: NULL handle or count");
+    return BBTC_EINVAL;
+  }
+  bbtc_opts opts;
+  BBTC_TRY(check_opts(opts_in, &opts));
+  DeviceGuard dg(g->device);
+  const int p = opts.p == 0 ? default_p(g) : opts.p;
+  cudaStream_t s = opts.stream ? (cudaStream_t)opts.stream : g->stream;
+  if (opts.device_budget_bytes != 0) {
+    const uint64_t need = g->bytes + (uint64_t)g->m * 12;
+    if (opts.device_budget_bytes < need) {
+      set_error("bbtc_count: a device budget of %llu bytes cannot hold the graph's blocks "
+                "(%llu bytes)", (unsigned long long)opts.device_budget_bytes,
+                (unsigned long long)need);
+      return BBTC_ENOMEM;
+    }
+  }
+  const bool rebuild = !(g->plan.p == p && g->plan.kernel_mode == opts.kernel &&
+                         g->plan.hash_threshold == opts.hash_threshold);
+  if (rebuild) BBTC_CUDA(cudaEventRecord(g->ev[2], s));
+  BBTC_TRY(build_plan(g, p, opts.kernel, opts.hash_threshold, s));
+  if (rebuild) BBTC_CUDA(cudaEventRecord(g->ev[3], s));
+  g->plan_timed = rebuild;
+  const Plan &pl = g->plan;
+  Scratch scratch(s);
+  CountOutputs out;
+  BBTC_TRY(scratch.get(&out.task_count, pl.ntasks));
+  BBTC_TRY(scratch.get(&out.total, 1));
+  BBTC_TRY(scratch.get(&out.status, 1));
+  if (opts.per_vertex_out) BBTC_TRY(scratch.get(&out.vertex_count, g->n));
+  BBTC_TRY(run_count(g, pl, out, opts.timeout_ms, s, g->ev[4], g->ev[5]));
+  unsigned long long total = 0;
+  int32_t status = 0;
+  BBTC_CUDA(cudaMemcpyAsync(&total, out.total, sizeof(total), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaMemcpyAsync(&status, out.status, sizeof(status), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  if (status != 0) {
+    set_error("bbtc_count: the counting kernel passed its %u ms limit", opts.timeout_ms);
+    return BBTC_ETIMEOUT;
+  }
+  const bool out_dev = (opts.flags & BBTC_OUT_DEVICE) != 0;
+  const cudaMemcpyKind kind = out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (opts.per_task_out)
+    BBTC_CUDA(cudaMemcpyAsync(opts.per_task_out, out.task_count,
+                              sizeof(uint64_t) * (size_t)pl.ntasks, kind, s));
+  if (opts.per_vertex_out && g->n > 0) {
+    unsigned long long *by_id = nullptr;
+    BBTC_TRY(scratch.get(&by_id, g->n));
+    k_scatter_by_perm<<<grid_for(g->n, 256, 16), 256, 0, s>>>(out.vertex_count, g->perm, g->n,
+                                                              by_id);
+    BBTC_LAUNCH_CHECK();
+    BBTC_CUDA(cudaMemcpyAsync(opts.per_vertex_out, by_id, sizeof(uint64_t) * (size_t)g->n, kind,
+                              s));
+  }
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  *count = total;
+  return BBTC_OK;
+}
+
+bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts *opts,
+                             uint64_t *counts, bbtc_status *per_graph) {
+  clear_error();
+  if (ng < 0 || (ng > 0 && (!gs || !counts))) {
+    set_error("bbtc_count_batch: invalid arguments");
+    return BBTC_EINVAL;
+  }
+  bbtc_opts o;
+  BBTC_TRY(check_opts(opts, &o));
+  o.per_task_out = nullptr;
+  o.per_vertex_out = nullptr;
+  bbtc_status first = BBTC_OK;
+  for (int32_t i = 0; i < ng; ++i) {
+    uint64_t c = 0;
+    bbtc_status st = gs[i] ? bbtc_count(gs[i], &o, &c) : BBTC_EINVAL;
+    if (per_graph) per_graph[i] = st;
+    if (st == BBTC_OK) counts[i] = c;
+    else if (first == BBTC_OK) first = st;
+  }
+  return first;
+}
+
+bbtc_status bbtc_graph_get_info(bbtc_graph_t g, bbtc_graph_info *info) {
+  clear_error();
+  if (!g || !info) {
+    set_error("bbtc_graph_get_info: NULL argument");
+    return BBTC_EINVAL;
+  }
+  info->n = g->n;
+  info->m = g->m;
+  info->dplus_max = g->dplus_max;
+  info->deg_max = g->deg_max;
+  info->device_bytes = g->bytes + g->plan.bytes;
+  if (!g->wedges_known) {
+    DeviceGuard dg(g->device);
+    BBTC_TRY(wedge_sums(g, &g->wedges_in, &g->wedges_out, g->stream));
+    g->wedges_known = true;
+  }
+  info->wedges_in = g->wedges_in;
+  info->wedges_out = g->wedges_out;
+  return BBTC_OK;
+}
+
+bbtc_status bbtc_graph_get_timings(bbtc_graph_t g, bbtc_timings *t) {
+  clear_error();
+  if (!g || !t) {
+    set_error("bbtc_graph_get_timings: NULL argument");
+    return BBTC_EINVAL;
+  }
+  DeviceGuard dg(g->device);
+  auto elapsed = [](cudaEvent_t a, cudaEvent_t b) -> double {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+      cudaGetLastError();
+      return 0.0;
+    }
+    return (double)ms;
+  };
+  t->prep_ms = elapsed(g->ev[0], g->ev[1]);
+  t->plan_ms = g->plan_timed ? elapsed(g->ev[2], g->ev[3]) : 0.0;
+  t->count_ms = elapsed(g->ev[4], g->ev[5]);
+  t->work_items = g->plan.nitems;
+  return BBTC_OK;
+}
+
+uint64_t bbtc_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+bbtc_status bbtc_graph_get_oriented(bbtc_graph_t g, int64_t *rowptr, int32_t *colidx,
+                                    int32_t *perm, int64_t *degree) {
+  clear_error();
+  if (!g) {
+    set_error("bbtc_graph_get_oriented: NULL handle");
+    return BBTC_EINVAL;
+  }
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->stream;
+  if (rowptr)
+    BBTC_CUDA(cudaMemcpyAsync(rowptr, g->rowptr, sizeof(int64_t) * (size_t)(g->n + 1),
+                              cudaMemcpyDeviceToHost, s));
+  if (colidx && g->m > 0)
+    BBTC_CUDA(cudaMemcpyAsync(colidx, g->colidx, sizeof(int32_t) * (size_t)g->m,
+                              cudaMemcpyDeviceToHost, s));
+  if (perm && g->n > 0)
+    BBTC_CUDA(cudaMemcpyAsync(perm, g->perm, sizeof(int32_t) * (size_t)g->n,
+                              cudaMemcpyDeviceToHost, s));
+  int32_t *deg32 = nullptr;
+  if (degree && g->n > 0) {
+    deg32 = new (std::nothrow) int32_t[(size_t)g->n];
+    if (!deg32) {
+      set_error("bbtc_graph_get_oriented: host allocation failed");
+      return BBTC_ENOMEM;
+    }
+    if (cudaMemcpyAsync(deg32, g->deg, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess) {
+      delete[] deg32;
+      set_error("bbtc_graph_get_oriented: copy failed");
+      return BBTC_ECUDA;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (deg32) {
+    for (int64_t v = 0; v < g->n; ++v) degree[v] = deg32[v];
+    delete[] deg32;
+  }
+  if (e != cudaSuccess) {
+    set_error("bbtc_graph_get_oriented: %s", cudaGetErrorString(e));
+    return BBTC_ECUDA;
+  }
+  return BBTC_OK;
+}
+
+bbtc_status bbtc_graph_get_plan(bbtc_graph_t g, int32_t p, int32_t *cuts, int64_t *block_nnz,
+                                int32_t *tasks, double *estimate, int32_t *order) {
+  clear_error();
+  if (!g || p < 1 || p > 64) {
+    set_error("bbtc_graph_get_plan: NULL handle or p outside 1..64");
+    return BBTC_EINVAL;
+  }
+  DeviceGuard dg(g->device);
+  cudaStream_t s = g->stream;
+  const int kmode = g->plan.p == p ? g->plan.kernel_mode : BBTC_KERNEL_AUTO;
+  const int thr = g->plan.p == p ? g->plan.hash_threshold : 16;
+  BBTC_TRY(build_plan(g, p, kmode, thr, s));
+  const Plan &pl = g->plan;
+  if (cuts)
+    BBTC_CUDA(cudaMemcpyAsync(cuts, pl.cuts, sizeof(int32_t) * (size_t)(p + 1),
+                              cudaMemcpyDeviceToHost, s));
+  int64_t *boff = nullptr;
+  if (block_nnz) {
+    boff = new (std::nothrow) int64_t[(size_t)p * (p + 1)];
+    if (!boff) {
+      set_error("bbtc_graph_get_plan: host allocation failed");
+      return BBTC_ENOMEM;
+    }
+    if (cudaMemcpyAsync(boff, pl.boff, sizeof(int64_t) * (size_t)p * (p + 1),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+      delete[] boff;
+      set_error("bbtc_graph_get_plan: copy failed");
+      return BBTC_ECUDA;
+    }
+  }
+  if (tasks)
+    BBTC_CUDA(cudaMemcpyAsync(tasks, pl.tasks, sizeof(int32_t) * 3 * (size_t)pl.ntasks,
+                              cudaMemcpyDeviceToHost, s));
+  if (estimate)
+    BBTC_CUDA(cudaMemcpyAsync(estimate, pl.est, sizeof(double) * (size_t)pl.ntasks,
+                              cudaMemcpyDeviceToHost, s));
+  if (order)
+    BBTC_CUDA(cudaMemcpyAsync(order, pl.order, sizeof(int32_t) * (size_t)pl.ntasks,
+                              cudaMemcpyDeviceToHost, s));
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (boff) {
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j)
+        block_nnz[i * p + j] = boff[i * (p + 1) + j + 1] - boff[i * (p + 1) + j];
+    delete[] boff;
+  }
+  if (e != cudaSuccess) {
+    set_error("bbtc_graph_get_plan: %s", cudaGetErrorString(e));
+    return BBTC_ECUDA;
+  }
+  return BBTC_OK;
+}
+
+}  // extern "C"

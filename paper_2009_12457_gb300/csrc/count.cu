@@ -1,0 +1,248 @@
+// count.cu -- per-task triangle counting (a9) and the reduction of the
+// per-task counts (a10).
+//
+// A task t = (i, j, k) counts, for every edge (u, v) of G_ij, the common
+// elements of N(G_ik, u) and N(G_jk, v) (Sec. 4.3, Alg. 5 / Alg. 6). The
+// kernel walks G_ij's edges grouped by their destination v (the in-edges of
+// each v in V_j that come from V_i, one contiguous range per block) and, for
+// each, looks up the elements of N(G_ik, u) that lie above v in N(G_jk, v).
+// Elements of N(G_ik, u) at or below v cannot be in N(G_jk, v) (every entry
+// of N(v) is above v), so the count equals Alg. 5's |N(G_ik,u) ∩ N(G_jk,v)|.
+//
+// Work: a persistent grid; each warp takes work items (task, in-edge range)
+// from a global counter, heaviest task first, until none remain.
+#include "graph.cuh"
+#include "primitives.cuh"
+
+namespace bbtc {
+
+namespace {
+
+constexpr int CT_NT = 256;
+constexpr int MAXP = 64;
+
+struct CountParams {
+  const int64_t *rowptr;
+  const int32_t *colidx;
+  const int32_t *ie_u;
+  const int32_t *ie_v;
+  const uint32_t *ie_e;
+  const int32_t *cuts;
+  int p;
+  const int32_t *tasks;
+  const WorkItem *items;
+  int64_t nitems;
+  unsigned long long *head;
+  unsigned long long *task_count;
+  unsigned long long *vcount;
+  int32_t *status;
+  uint64_t timeout_ns;
+};
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <bool PER_VERTEX>
+__global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
+  __shared__ int32_t cuts[MAXP + 1];
+  for (int i = threadIdx.x; i <= P.p; i += CT_NT) cuts[i] = P.cuts[i];
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t t_start = P.timeout_ns ? global_ns() : 0;
+  const int64_t *__restrict__ rowptr = P.rowptr;
+  const int32_t *__restrict__ col = P.colidx;
+
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(P.head, 1ull);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (unsigned long long)P.nitems) break;
+    if (P.timeout_ns && global_ns() - t_start > P.timeout_ns) {
+      if (lane == 0) atomicExch(P.status, 1);
+      break;
+    }
+    const WorkItem w = P.items[it];
+    const int t = w.task;
+    const int j = P.tasks[3 * t + 1], k = P.tasks[3 * t + 2];
+    const int32_t ck = cuts[k], ck1 = cuts[k + 1];
+    unsigned long long acc = 0;
+
+    for (int64_t base = w.x0; base < w.x1; base += 32) {
+      const int64_t x = base + lane;
+      int64_t s0 = 0, s1 = 0, b0 = 0, b1 = 0;
+      int32_t u = 0, v = 0;
+      if (x < w.x1) {
+        u = P.ie_u[x];
+        v = P.ie_v[x];
+        const int64_t e = P.ie_e[x];
+        const int64_t ru1 = rowptr[u + 1];
+        // N(G_ik, u) restricted to entries above v
+        s0 = (k == j) ? e + 1 : lower_bound_dev<int32_t, int64_t>(col, rowptr[u], ru1, ck);
+        s1 = lower_bound_dev<int32_t, int64_t>(col, s0, ru1, ck1);
+        // N(G_jk, v)
+        const int64_t rv1 = rowptr[v + 1];
+        b0 = lower_bound_dev<int32_t, int64_t>(col, rowptr[v], rv1, ck);
+        b1 = lower_bound_dev<int32_t, int64_t>(col, b0, rv1, ck1);
+        if (b1 == b0) s1 = s0;
+      }
+      const uint32_t len = (uint32_t)(s1 - s0);
+      const uint32_t incl = warp_inclusive_scan(len);
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t excl = incl - len;
+      for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        // owner: the last lane whose exclusive prefix is <= q
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          uint32_t ex = __shfl_sync(0xffffffffu, excl, o + step);
+          if (ex <= q) o += step;
+        }
+        const int64_t so = __shfl_sync(0xffffffffu, s0, o);
+        const int64_t bo0 = __shfl_sync(0xffffffffu, b0, o);
+        const int64_t bo1 = __shfl_sync(0xffffffffu, b1, o);
+        const uint32_t exo = __shfl_sync(0xffffffffu, excl, o);
+        int32_t uo = 0, vo = 0;
+        if (PER_VERTEX) {
+          uo = __shfl_sync(0xffffffffu, u, o);
+          vo = __shfl_sync(0xffffffffu, v, o);
+        }
+        if (q < total) {
+          const int32_t wv = col[so + (q - exo)];
+          const int64_t pos = lower_bound_dev<int32_t, int64_t>(col, bo0, bo1, wv);
+          if (pos < bo1 && col[pos] == wv) {
+            ++acc;
+            if (PER_VERTEX) {
+              atomicAdd(&P.vcount[uo], 1ull);
+              atomicAdd(&P.vcount[vo], 1ull);
+              atomicAdd(&P.vcount[wv], 1ull);
+            }
+          }
+        }
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0 && acc) atomicAdd(&P.task_count[t], acc);
+  }
+}
+
+__global__ void k_sum_u64(const unsigned long long *__restrict__ in, int64_t count,
+                          unsigned long long *__restrict__ out) {
+  unsigned long long s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += in[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+__global__ void k_wedges(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                         const int32_t *__restrict__ esrc, int64_t m, int64_t n,
+                         unsigned long long *__restrict__ sums) {
+  unsigned long long win = 0, wout = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int32_t v = colidx[e];
+    win += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+  }
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+    const unsigned long long d = (unsigned long long)(rowptr[u + 1] - rowptr[u]);
+    wout += d * (d > 0 ? d - 1 : 0) / 2;
+  }
+  win = warp_sum(win);
+  wout = warp_sum(wout);
+  if ((threadIdx.x & 31) == 0) {
+    if (win) atomicAdd(&sums[0], win);
+    if (wout) atomicAdd(&sums[1], wout);
+  }
+}
+
+int g_count_blocks[2] = {0, 0};
+
+}  // namespace
+
+bbtc_status wedge_sums(const bbtc_graph *g, uint64_t *in_sum, uint64_t *out_sum,
+                       cudaStream_t s) {
+  Scratch scratch(s);
+  unsigned long long *sums = nullptr;
+  BBTC_TRY(scratch.get(&sums, 2));
+  BBTC_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), s));
+  const int64_t work = g->m > g->n ? g->m : g->n;
+  if (work > 0) {
+    k_wedges<<<grid_for(work, 256, 16), 256, 0, s>>>(g->rowptr, g->colidx, g->esrc, g->m, g->n,
+                                                     sums);
+    BBTC_LAUNCH_CHECK();
+  }
+  unsigned long long h[2] = {0, 0};
+  BBTC_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  *in_sum = h[0];
+  *out_sum = h[1];
+  return BBTC_OK;
+}
+
+bbtc_status run_count(bbtc_graph *g, const Plan &pl, const CountOutputs &out,
+                      uint32_t timeout_ms, cudaStream_t s, cudaEvent_t ev_begin,
+                      cudaEvent_t ev_end) {
+  const int64_t nt = pl.ntasks;
+  BBTC_CUDA(cudaMemsetAsync(out.task_count, 0, sizeof(unsigned long long) * (size_t)nt, s));
+  BBTC_CUDA(cudaMemsetAsync(out.total, 0, sizeof(unsigned long long), s));
+  BBTC_CUDA(cudaMemsetAsync(out.status, 0, sizeof(int32_t), s));
+  if (out.vertex_count)
+    BBTC_CUDA(cudaMemsetAsync(out.vertex_count, 0,
+                              sizeof(unsigned long long) * (size_t)(g->n > 0 ? g->n : 1), s));
+  if (pl.nitems > 0) {
+    Scratch scratch(s);
+    unsigned long long *head = nullptr;
+    BBTC_TRY(scratch.get(&head, 1));
+    BBTC_CUDA(cudaMemsetAsync(head, 0, sizeof(unsigned long long), s));
+    CountParams P;
+    P.rowptr = g->rowptr;
+    P.colidx = g->colidx;
+    P.ie_u = pl.ie_u;
+    P.ie_v = pl.ie_v;
+    P.ie_e = pl.ie_e;
+    P.cuts = pl.cuts;
+    P.p = pl.p;
+    P.tasks = pl.tasks;
+    P.items = pl.items;
+    P.nitems = pl.nitems;
+    P.head = head;
+    P.task_count = out.task_count;
+    P.vcount = out.vertex_count;
+    P.status = out.status;
+    P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
+    const bool pv = out.vertex_count != nullptr;
+    int &blocks_per_sm = g_count_blocks[pv];
+    if (!blocks_per_sm) {
+      if (pv)
+        BBTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_count<true>,
+                                                                CT_NT, 0));
+      else
+        BBTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_count<false>,
+                                                                CT_NT, 0));
+      if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    int64_t blocks = (int64_t)num_sms() * blocks_per_sm;
+    const int64_t need = (pl.nitems + CT_NT / 32 - 1) / (CT_NT / 32);
+    if (blocks > need) blocks = need;
+    if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
+    if (pv)
+      k_count<true><<<(unsigned)blocks, CT_NT, 0, s>>>(P);
+    else
+      k_count<false><<<(unsigned)blocks, CT_NT, 0, s>>>(P);
+    BBTC_LAUNCH_CHECK();
+    if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
+  } else {
+    if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
+    if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
+  }
+  k_sum_u64<<<grid_for(nt, 256, 2), 256, 0, s>>>(out.task_count, nt, out.total);
+  BBTC_LAUNCH_CHECK();
+  return BBTC_OK;
+}
+
+}  // namespace bbtc

@@ -1,0 +1,92 @@
+// graph.cuh -- the graph handle and the per-p plan it caches.
+#pragma once
+
+#include "common.cuh"
+
+namespace bbtc {
+
+// One unit of counting work: the in-edges [x0, x1) of block G_ij (grouped by
+// destination v) for task t = (i, j, k).
+struct WorkItem {
+  int32_t task;
+  int32_t flags;  // bit 0: staged lists use the hash table (bbTC-HMap), else sorted search
+  int64_t x0, x1;
+};
+
+// Everything bbtc_count builds for one p (Sec. 2 partition, Sec. 4.2 tasks,
+// Sec. 5 estimate and order), cached on the handle until p changes.
+struct Plan {
+  int p = 0;
+  int64_t ntasks = 0;
+  int32_t *cuts = nullptr;      // p+1
+  int32_t *ie_u = nullptr;      // m: in-edges sorted by (part(u), v, u): source u
+  int32_t *ie_v = nullptr;      // m: destination v
+  uint32_t *ie_e = nullptr;     // m: position of the edge (u,v) in the oriented CSR
+  int64_t *boff = nullptr;      // p*(p+1): block (i,j) in-edges = [boff[i*(p+1)+j], +1)
+  int32_t *tasks = nullptr;     // 3*T: (i,j,k) in Alg. 4 order
+  double *est = nullptr;        // T: ExecTime in Alg. 4 order
+  int32_t *order = nullptr;     // T: task indices by non-increasing estimate
+  int64_t nitems = 0;
+  WorkItem *items = nullptr;    // work items, heaviest task first
+  int32_t kernel_mode = -1;     // bbtc_kernel the items were built for
+  int32_t hash_threshold = 0;
+  uint64_t bytes = 0;
+};
+
+}  // namespace bbtc
+
+struct bbtc_graph {
+  int64_t n = 0;
+  int64_t m = 0;
+  int nb = 1;                  // bits per vertex id: 2^nb >= n
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t *rowptr = nullptr;   // oriented CSR (degree-order positions), n+1
+  int32_t *colidx = nullptr;   // m, rows sorted ascending
+  int32_t *esrc = nullptr;     // m, source position of each oriented edge
+  int32_t *perm = nullptr;     // n, perm[r] = original id at position r
+  int32_t *deg = nullptr;      // n, undirected simple degree by original id
+  int64_t dplus_max = 0;
+  int64_t deg_max = 0;
+  uint64_t bytes = 0;
+  bbtc::Plan plan;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool plan_timed = false;
+  bool wedges_known = false;
+  uint64_t wedges_in = 0, wedges_out = 0;
+};
+
+namespace bbtc {
+
+// a1-a4: build g's oriented CSR from an input CSR already on the device.
+bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t *d_colidx,
+                          int64_t nnz, bool symmetric);
+
+// a5-a8: partition, blocks, tasks, estimate, order and work items for p.
+bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold,
+                       cudaStream_t s);
+void free_plan(Plan *pl, cudaStream_t s);
+
+// a9-a10: per-task counts (device, Alg. 4 order) and optional per-vertex
+// counts by position; *total_dev receives the sum.
+struct CountOutputs {
+  unsigned long long *task_count = nullptr;  // device, T
+  unsigned long long *vertex_count = nullptr;  // device, n (by position) or null
+  unsigned long long *total = nullptr;  // device, 1
+  int32_t *status = nullptr;            // device, 1: 0 ok, 1 timeout
+};
+bbtc_status run_count(bbtc_graph *g, const Plan &pl, const CountOutputs &out,
+                      uint32_t timeout_ms, cudaStream_t s, cudaEvent_t ev_begin,
+                      cudaEvent_t ev_end);
+
+// Work figures of the oriented graph (device): sum_{(u,v)} d+(v) and
+// sum_u d+(u)(d+(u)-1)/2.
+bbtc_status wedge_sums(const bbtc_graph *g, uint64_t *in_sum, uint64_t *out_sum,
+                       cudaStream_t s);
+
+// Default p when the caller passes 0 (Sec. 7.3: p near the average degree,
+// clamped for a single resident GPU).
+int default_p(const bbtc_graph *g);
+
+}  // namespace bbtc

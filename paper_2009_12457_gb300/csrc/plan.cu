@@ -1,0 +1,304 @@
+// plan.cu -- per-p planning steps of bbTC (run by bbtc_count, cached per p):
+//   a5 partition: contiguous cuts of the degree order balanced on oriented
+//      edges (Sec. 2 vertex partition V^p; Sec. 4.1 symmetric partition)
+//   a6 blocks G_ij = {(u,v) : u in V_i, v in V_j} (Sec. 2), materialised as
+//      the in-edges of each v grouped by the part of their source, so that a
+//      block's edges are one contiguous, destination-ordered range
+//   a7 task composition: all (i,j,k), i <= j <= k (Sec. 4.2, Alg. 4)
+//   a8 ExecTime estimate and non-increasing order (Sec. 5), split into work
+//      items of at most `chunk` in-edges each
+#include "graph.cuh"
+#include "primitives.cuh"
+
+namespace bbtc {
+
+namespace {
+
+constexpr int MAXP = 64;
+
+// c_0 = 0, c_p = n, c_i = min{ r : rowptr[r] >= ceil(i*m/p) }.
+__global__ void k_cuts(const int64_t *__restrict__ rowptr, int64_t n, int p,
+                       int32_t *__restrict__ cuts) {
+  const int i = threadIdx.x;
+  if (i > p) return;
+  const int64_t m = rowptr[n];
+  int32_t c;
+  if (i == 0) {
+    c = 0;
+  } else if (i == p) {
+    c = (int32_t)n;
+  } else {
+    int64_t target = ((int64_t)i * m + p - 1) / p;
+    c = (int32_t)lower_bound_dev<int64_t, int64_t>(rowptr, 0, n + 1, target);
+  }
+  cuts[i] = c;
+}
+
+// In-edge keys: (part(u) << nb) | v for the oriented edge e = (u, v), value e.
+__global__ void k_inedge_keys(const int32_t *__restrict__ colidx,
+                              const int32_t *__restrict__ esrc, int64_t m,
+                              const int32_t *__restrict__ cuts_g, int p, int nb,
+                              uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  __shared__ int32_t cuts[MAXP + 1];
+  for (int i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int part = part_of_dev(cuts, p, esrc[e]);
+    keys[e] = ((uint64_t)part << nb) | (uint64_t)colidx[e];
+    vals[e] = (uint32_t)e;
+  }
+}
+
+__global__ void k_inedge_finish(const uint64_t *__restrict__ keys,
+                                const uint32_t *__restrict__ vals, int64_t m, int nb,
+                                const int32_t *__restrict__ esrc, int32_t *__restrict__ ie_u,
+                                int32_t *__restrict__ ie_v, uint32_t *__restrict__ ie_e) {
+  const uint64_t mask = (1ull << nb) - 1ull;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t e = vals[x];
+    ie_v[x] = (int32_t)(keys[x] & mask);
+    ie_e[x] = e;
+    ie_u[x] = esrc[e];
+  }
+}
+
+// boff[i*(p+1)+j] = first in-edge of part i whose destination is >= c_j.
+__global__ void k_block_offsets(const uint64_t *__restrict__ keys, int64_t m,
+                                const int32_t *__restrict__ cuts, int p, int nb,
+                                int64_t *__restrict__ boff) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p * (p + 1)) return;
+  const int i = idx / (p + 1), j = idx % (p + 1);
+  const uint64_t target = ((uint64_t)i << nb) + (uint64_t)cuts[j];
+  boff[idx] = lower_bound_dev<uint64_t, int64_t>(keys, 0, m, target);
+}
+
+__device__ __forceinline__ int64_t block_nnz(const int64_t *boff, int p, int i, int j) {
+  return boff[i * (p + 1) + j + 1] - boff[i * (p + 1) + j];
+}
+
+// Alg. 4 order: index of (i, j, j) is the number of tasks with a smaller first
+// index plus those with first index i and a smaller second index.
+__device__ __forceinline__ int64_t task_index(int p, int i, int j, int k) {
+  int64_t t = 0;
+  for (int a = 0; a < i; ++a) t += (int64_t)(p - a) * (p - a + 1) / 2;
+  for (int b = i; b < j; ++b) t += p - b;
+  return t + (k - j);
+}
+
+// a7 + a8: tasks, ExecTime (Sec. 5) and the sort keys of the order.
+// est = |G_ij| * max(delta(G_ik), delta(G_jk)), delta(G_ab) = |G_ab| / |V_a|.
+__global__ void k_tasks(const int64_t *__restrict__ boff, const int32_t *__restrict__ cuts,
+                        int p, int32_t *__restrict__ tasks, double *__restrict__ est,
+                        uint64_t *__restrict__ order_keys, uint32_t *__restrict__ order_vals) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per (i, j, k)
+  if (idx >= p * p * p) return;
+  const int i = idx / (p * p), j = (idx / p) % p, k = idx % p;
+  if (!(i <= j && j <= k)) return;
+  const int64_t t = task_index(p, i, j, k);
+  tasks[3 * t + 0] = i;
+  tasks[3 * t + 1] = j;
+  tasks[3 * t + 2] = k;
+  const int64_t vi = cuts[i + 1] - cuts[i], vj = cuts[j + 1] - cuts[j];
+  const double dik = vi > 0 ? (double)block_nnz(boff, p, i, k) / (double)vi : 0.0;
+  const double djk = vj > 0 ? (double)block_nnz(boff, p, j, k) / (double)vj : 0.0;
+  const double e = (double)block_nnz(boff, p, i, j) * (dik > djk ? dik : djk);
+  est[t] = e;
+  // non-negative doubles order like their bit patterns; complement for
+  // descending, and the stable sort keeps Alg. 4 order among equal estimates
+  order_keys[t] = ~(uint64_t)__double_as_longlong(e);
+  order_vals[t] = (uint32_t)t;
+}
+
+__global__ void k_order_finish(const uint32_t *__restrict__ vals, int64_t nt,
+                               int32_t *__restrict__ order) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nt;
+       x += (int64_t)gridDim.x * blockDim.x)
+    order[x] = (int32_t)vals[x];
+}
+
+// Number of work items of the task at each position of the order. A task
+// whose G_ij, G_ik or G_jk is empty holds no triangle and gets none.
+__global__ void k_item_counts(const int32_t *__restrict__ order,
+                              const int32_t *__restrict__ tasks, const int64_t *__restrict__ boff,
+                              int p, int64_t nt, int64_t chunk, uint64_t *__restrict__ counts) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nt;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int t = order[x];
+    const int i = tasks[3 * t], j = tasks[3 * t + 1], k = tasks[3 * t + 2];
+    const int64_t nij = block_nnz(boff, p, i, j);
+    const bool empty = nij == 0 || block_nnz(boff, p, i, k) == 0 || block_nnz(boff, p, j, k) == 0;
+    counts[x] = empty ? 0 : (uint64_t)((nij + chunk - 1) / chunk);
+  }
+}
+
+__global__ void k_item_fill(const int32_t *__restrict__ order, const int32_t *__restrict__ tasks,
+                            const int64_t *__restrict__ boff, const int32_t *__restrict__ cuts,
+                            int p, int64_t nt, int64_t chunk, const uint64_t *__restrict__ first,
+                            int kernel_mode, int32_t hash_threshold,
+                            WorkItem *__restrict__ items) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nt;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t n_items = first[x + 1] - first[x];
+    if (n_items == 0) continue;
+    const int t = order[x];
+    const int i = tasks[3 * t], j = tasks[3 * t + 1], k = tasks[3 * t + 2];
+    const int64_t b0 = boff[i * (p + 1) + j], b1 = boff[i * (p + 1) + j + 1];
+    // isDense (Alg. 7): staged lists N(G_jk, v) averaging more than the
+    // threshold use the hash table, shorter ones sorted search.
+    int32_t flags;
+    if (kernel_mode == BBTC_KERNEL_HASHMAP) {
+      flags = 1;
+    } else if (kernel_mode == BBTC_KERNEL_INTERSECT) {
+      flags = 0;
+    } else {
+      const int64_t vj = cuts[j + 1] - cuts[j];
+      const double djk = vj > 0 ? (double)block_nnz(boff, p, j, k) / (double)vj : 0.0;
+      flags = djk > (double)hash_threshold ? 1 : 0;
+    }
+    for (uint64_t c = 0; c < n_items; ++c) {
+      WorkItem w;
+      w.task = t;
+      w.flags = flags;
+      w.x0 = b0 + (int64_t)c * chunk;
+      w.x1 = w.x0 + chunk < b1 ? w.x0 + chunk : b1;
+      items[first[x] + c] = w;
+    }
+  }
+}
+
+}  // namespace
+
+void free_plan(Plan *pl, cudaStream_t s) {
+  dfree(pl->cuts, s);
+  dfree(pl->ie_u, s);
+  dfree(pl->ie_v, s);
+  dfree(pl->ie_e, s);
+  dfree(pl->boff, s);
+  dfree(pl->tasks, s);
+  dfree(pl->est, s);
+  dfree(pl->order, s);
+  dfree(pl->items, s);
+  *pl = Plan();
+}
+
+int default_p(const bbtc_graph *g) {
+  // Sec. 7.3 suggests p near the average degree for a CPU cache; on one GPU
+  // with the whole graph resident, fewer and larger blocks keep the per-task
+  // overheads small. Grow p slowly with m.
+  if (g->m < (1 << 16)) return 1;
+  if (g->m < (1 << 22)) return 2;
+  if (g->m < (1 << 27)) return 4;
+  return 8;
+}
+
+bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold,
+                       cudaStream_t s) {
+  if (g->plan.p == p && g->plan.kernel_mode == kernel_mode &&
+      g->plan.hash_threshold == hash_threshold)
+    return BBTC_OK;
+  free_plan(&g->plan, s);
+  Plan pl;
+  pl.p = p;
+  pl.kernel_mode = kernel_mode;
+  pl.hash_threshold = hash_threshold;
+  pl.ntasks = (int64_t)p * (p + 1) * (p + 2) / 6;
+  const int64_t n = g->n, m = g->m;
+  const int nb = g->nb;
+  Scratch scratch(s);
+  bbtc_status st = BBTC_OK;
+#define PLAN_TRY(expr)          \
+  do {                          \
+    st = (expr);                \
+    if (st != BBTC_OK) {        \
+      free_plan(&pl, s);        \
+      return st;                \
+    }                           \
+  } while (0)
+
+  // a5: cuts
+  PLAN_TRY(dalloc_n(&pl.cuts, p + 1, s));
+  k_cuts<<<1, MAXP + 1, 0, s>>>(g->rowptr, n, p, pl.cuts);
+  PLAN_TRY(launch_status("build_plan"));
+
+  // a6: in-edges grouped by (part(u), v, u) and the block offsets
+  uint64_t *ka = nullptr, *kb = nullptr;
+  uint32_t *va = nullptr, *vb = nullptr;
+  PLAN_TRY(scratch.get(&ka, m));
+  PLAN_TRY(scratch.get(&kb, m));
+  PLAN_TRY(scratch.get(&va, m));
+  PLAN_TRY(scratch.get(&vb, m));
+  PLAN_TRY(dalloc_n(&pl.ie_u, m, s));
+  PLAN_TRY(dalloc_n(&pl.ie_v, m, s));
+  PLAN_TRY(dalloc_n(&pl.ie_e, m, s));
+  PLAN_TRY(dalloc_n(&pl.boff, (int64_t)p * (p + 1), s));
+  const int pbits = ceil_log2_u64((uint64_t)p);
+  bool in_alt = false;
+  if (m > 0) {
+    k_inedge_keys<<<grid_for(m, 256, 32), 256, 0, s>>>(g->colidx, g->esrc, m, pl.cuts, p, nb,
+                                                        ka, va);
+    PLAN_TRY(launch_status("build_plan"));
+    PLAN_TRY(radix_sort(ka, kb, va, vb, m, 0, nb + pbits, s, &in_alt));
+    k_inedge_finish<<<grid_for(m, 256, 32), 256, 0, s>>>(in_alt ? kb : ka, in_alt ? vb : va, m,
+                                                          nb, g->esrc, pl.ie_u, pl.ie_v, pl.ie_e);
+    PLAN_TRY(launch_status("build_plan"));
+  }
+  k_block_offsets<<<(p * (p + 1) + 127) / 128, 128, 0, s>>>(in_alt ? kb : ka, m, pl.cuts, p, nb,
+                                                            pl.boff);
+  PLAN_TRY(launch_status("build_plan"));
+
+  // a7 + a8: tasks, estimates, order
+  const int64_t nt = pl.ntasks;
+  PLAN_TRY(dalloc_n(&pl.tasks, 3 * nt, s));
+  PLAN_TRY(dalloc_n(&pl.est, nt, s));
+  PLAN_TRY(dalloc_n(&pl.order, nt, s));
+  uint64_t *okeys = ka, *okeys_alt = kb;  // reuse (m may be < nt: allocate if needed)
+  uint32_t *ovals = va, *ovals_alt = vb;
+  if (nt > m) {
+    PLAN_TRY(scratch.get(&okeys, nt));
+    PLAN_TRY(scratch.get(&okeys_alt, nt));
+    PLAN_TRY(scratch.get(&ovals, nt));
+    PLAN_TRY(scratch.get(&ovals_alt, nt));
+  }
+  k_tasks<<<(p * p * p + 127) / 128, 128, 0, s>>>(pl.boff, pl.cuts, p, pl.tasks, pl.est, okeys,
+                                                  ovals);
+  PLAN_TRY(launch_status("build_plan"));
+  PLAN_TRY(radix_sort(okeys, okeys_alt, ovals, ovals_alt, nt, 0, 64, s, &in_alt));
+  k_order_finish<<<grid_for(nt, 256, 4), 256, 0, s>>>(in_alt ? ovals_alt : ovals, nt, pl.order);
+  PLAN_TRY(launch_status("build_plan"));
+
+  // work items: about 64 per resident warp in total, 64..4096 in-edges each
+  const int64_t warps = (int64_t)num_sms() * 48;
+  int64_t chunk = (m * (int64_t)(p < 3 ? p : 3)) / (warps * 64);
+  chunk = chunk < 64 ? 64 : (chunk > 4096 ? 4096 : chunk);
+  uint64_t *first = nullptr;
+  PLAN_TRY(scratch.get(&first, nt + 1));
+  k_item_counts<<<grid_for(nt, 256, 4), 256, 0, s>>>(pl.order, pl.tasks, pl.boff, p, nt, chunk,
+                                                     first);
+  PLAN_TRY(launch_status("build_plan"));
+  PLAN_TRY(exclusive_scan_u64(first, first, nt + 1, s));
+  uint64_t nitems = 0;
+  if (cudaMemcpyAsync(&nitems, first + nt, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("build_plan: reading the work-item count failed");
+    free_plan(&pl, s);
+    return BBTC_ECUDA;
+  }
+  pl.nitems = (int64_t)nitems;
+  PLAN_TRY(dalloc_n(&pl.items, pl.nitems, s));
+  if (nitems > 0) {
+    k_item_fill<<<grid_for(nt, 256, 4), 256, 0, s>>>(pl.order, pl.tasks, pl.boff, pl.cuts, p, nt,
+                                                     chunk, first, kernel_mode, hash_threshold,
+                                                     pl.items);
+    PLAN_TRY(launch_status("build_plan"));
+  }
+#undef PLAN_TRY
+  pl.bytes = (uint64_t)m * 12 + (uint64_t)nt * 24 + (uint64_t)pl.nitems * sizeof(WorkItem);
+  g->plan = pl;
+  return BBTC_OK;
+}
+
+}  // namespace bbtc

@@ -1,0 +1,311 @@
+// prep.cu -- graph-only steps of bbTC (run once per graph by bbtc_graph_create):
+//   a1 canonical simple edge set  (Sec. 2: simple undirected graph, (u,v) with u<v)
+//   a2 degree                     (Sec. 2, Sec. 4.1)
+//   a3 order by degree            (Sec. 4.1: non-decreasing degree, ties by id)
+//   a4 orientation                (Sec. 2: N(G,u) = {v : (u,v) in E, u < v})
+#include "graph.cuh"
+#include "primitives.cuh"
+
+namespace bbtc {
+
+namespace {
+
+constexpr int EK_NT = 256;
+constexpr int EK_TILE = 2048;
+
+// rowptr[0] == 0 and non-decreasing; error bit 1 otherwise.
+__global__ void k_validate_rowptr(const int64_t *__restrict__ rowptr, int64_t n,
+                                  int32_t *__restrict__ err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (rowptr[i] > rowptr[i + 1]) atomicOr(err, 1);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && rowptr[0] != 0) atomicOr(err, 1);
+}
+
+// a1: one 64-bit key (min << nb) | max per input entry joining two different
+// vertices; self-loops (and, for symmetric input, entries with u > v) become
+// the sentinel, which sorts last and is dropped by the unique step.
+__global__ void __launch_bounds__(EK_NT) k_emit_keys(const int64_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ colidx,
+                                                     int64_t n, int64_t nnz, int nb,
+                                                     bool symmetric, uint64_t sentinel,
+                                                     uint64_t *__restrict__ keys,
+                                                     int32_t *__restrict__ err) {
+  __shared__ int64_t win[2];
+  const int64_t ntiles = (nnz + EK_TILE - 1) / EK_TILE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t t0 = tile * EK_TILE;
+    const int64_t t1 = t0 + EK_TILE < nnz ? t0 + EK_TILE : nnz;
+    if (threadIdx.x < 2) {
+      // last row r in [0, n) with rowptr[r] <= target
+      int64_t target = threadIdx.x == 0 ? t0 : t1 - 1;
+      int64_t lo = 0, hi = n;  // invariant: rowptr[lo] <= target
+      while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (rowptr[mid] <= target) lo = mid; else hi = mid;
+      }
+      win[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    const int64_t rlo = win[0], rhi = win[1];
+    for (int64_t idx = t0 + threadIdx.x; idx < t1; idx += EK_NT) {
+      int64_t lo = rlo, hi = rhi + 1;
+      while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (rowptr[mid] <= idx) lo = mid; else hi = mid;
+      }
+      const int64_t u = lo;
+      const int64_t v = colidx[idx];
+      uint64_t key = sentinel;
+      if (v < 0 || v >= n) {
+        atomicOr(err, 2);
+      } else if (v != u && !(symmetric && u > v)) {
+        uint64_t a = (uint64_t)(u < v ? u : v), b = (uint64_t)(u < v ? v : u);
+        key = (a << nb) | b;
+      }
+      keys[idx] = key;
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int UQ_NT = 512;
+constexpr int UQ_ITEMS = 8;
+constexpr int UQ_TILE = UQ_NT * UQ_ITEMS;
+
+__device__ __forceinline__ bool is_head(const uint64_t *keys, int64_t i, uint64_t sentinel) {
+  uint64_t k = keys[i];
+  return k != sentinel && (i == 0 || keys[i - 1] != k);
+}
+
+__global__ void __launch_bounds__(UQ_NT) k_unique_count(const uint64_t *__restrict__ keys,
+                                                        int64_t count, uint64_t sentinel,
+                                                        uint64_t *__restrict__ block_counts) {
+  __shared__ uint64_t tmp[UQ_NT / 32 + 1];
+  const int64_t base = (int64_t)blockIdx.x * UQ_TILE + (int64_t)threadIdx.x * UQ_ITEMS;
+  uint64_t c = 0;
+#pragma unroll
+  for (int i = 0; i < UQ_ITEMS; ++i)
+    if (base + i < count && is_head(keys, base + i, sentinel)) ++c;
+  uint64_t total;
+  block_exclusive_scan<uint64_t, UQ_NT>(c, tmp, &total);
+  if (threadIdx.x == 0) block_counts[blockIdx.x] = total;
+}
+
+// a1 + a2: compact the distinct keys and count each endpoint's degree.
+__global__ void __launch_bounds__(UQ_NT) k_unique_write(const uint64_t *__restrict__ keys,
+                                                        int64_t count, uint64_t sentinel,
+                                                        const uint64_t *__restrict__ block_off,
+                                                        int nb, uint64_t *__restrict__ ukeys,
+                                                        int32_t *__restrict__ deg) {
+  __shared__ uint64_t tmp[UQ_NT / 32 + 1];
+  const int64_t base = (int64_t)blockIdx.x * UQ_TILE + (int64_t)threadIdx.x * UQ_ITEMS;
+  bool head[UQ_ITEMS];
+  uint64_t c = 0;
+#pragma unroll
+  for (int i = 0; i < UQ_ITEMS; ++i) {
+    head[i] = base + i < count && is_head(keys, base + i, sentinel);
+    c += head[i];
+  }
+  uint64_t total;
+  uint64_t pos = block_exclusive_scan<uint64_t, UQ_NT>(c, tmp, &total) + block_off[blockIdx.x];
+  const uint64_t mask = (1ull << nb) - 1ull;
+#pragma unroll
+  for (int i = 0; i < UQ_ITEMS; ++i) {
+    if (head[i]) {
+      uint64_t k = keys[base + i];
+      ukeys[pos++] = k;
+      atomicAdd(&deg[k >> nb], 1);
+      atomicAdd(&deg[k & mask], 1);
+    }
+  }
+}
+
+// a3 keys: (degree << nb) | id, so ascending order is (degree, id).
+__global__ void k_rank_keys(const int32_t *__restrict__ deg, int64_t n, int nb,
+                            uint64_t *__restrict__ keys) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    keys[v] = ((uint64_t)deg[v] << nb) | (uint64_t)v;
+}
+
+__global__ void k_rank_finish(const uint64_t *__restrict__ sorted, int64_t n, int nb,
+                              int32_t *__restrict__ perm, int32_t *__restrict__ rank) {
+  const uint64_t mask = (1ull << nb) - 1ull;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = (int32_t)(sorted[r] & mask);
+    perm[r] = v;
+    rank[v] = (int32_t)r;
+  }
+}
+
+// a4 keys: each edge {a,b} as (min(rank) << nb) | max(rank).
+__global__ void k_orient_keys(const uint64_t *__restrict__ ukeys, int64_t m, int nb,
+                              const int32_t *__restrict__ rank, uint64_t *__restrict__ okeys) {
+  const uint64_t mask = (1ull << nb) - 1ull;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = ukeys[e];
+    uint64_t ra = (uint64_t)rank[k >> nb], rb = (uint64_t)rank[k & mask];
+    okeys[e] = ra < rb ? (ra << nb) | rb : (rb << nb) | ra;
+  }
+}
+
+// Oriented CSR from the sorted oriented keys: colidx, the source of each
+// edge, and the row lengths (counted into rowptr[src], warp-aggregated; a scan
+// turns them into offsets).
+__global__ void k_csr_finish(const uint64_t *__restrict__ okeys, int64_t m, int nb,
+                             int32_t *__restrict__ colidx, int32_t *__restrict__ esrc,
+                             unsigned long long *__restrict__ rowlen) {
+  const uint64_t mask = (1ull << nb) - 1ull;
+  const unsigned lane = threadIdx.x & 31u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+    const int64_t e = base + threadIdx.x;
+    const bool valid = e < m;
+    int64_t s = -1;
+    if (valid) {
+      uint64_t k = okeys[e];
+      s = (int64_t)(k >> nb);
+      colidx[e] = (int32_t)(k & mask);
+      esrc[e] = (int32_t)s;
+    }
+    unsigned peers = __match_any_sync(0xffffffffu, s);
+    if (valid && lane == (unsigned)(__ffs(peers) - 1))
+      atomicAdd(&rowlen[s], (unsigned long long)__popc(peers));
+  }
+}
+
+}  // namespace
+
+bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t *d_colidx,
+                          int64_t nnz, bool symmetric) {
+  cudaStream_t s = g->stream;
+  const int64_t n = g->n;
+  const int nb = ceil_log2_u64((uint64_t)n) < 1 ? 1 : ceil_log2_u64((uint64_t)n);
+  g->nb = nb;
+  Scratch scratch(s);
+  int32_t *err = nullptr;
+  int64_t *hstats = nullptr;  // device: [0]=m, [1]=deg_max, [2]=err
+  BBTC_TRY(scratch.get(&err, 1));
+  BBTC_TRY(scratch.get(&hstats, 3));
+  BBTC_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+
+  // ---- validation of rowptr (colidx range is checked while emitting keys)
+  if (n > 0) {
+    k_validate_rowptr<<<grid_for(n, 256, 8), 256, 0, s>>>(d_rowptr, n, err);
+    BBTC_LAUNCH_CHECK();
+  }
+
+  // ---- a1: canonical keys, sort, unique; a2: degree
+  const uint64_t sentinel = (nb * 2 >= 64) ? ~0ull : ((1ull << (2 * nb)) - 1ull);
+  uint64_t *ka = nullptr, *kb = nullptr;
+  const int64_t kcap = nnz > n ? nnz : n;  // buffers are reused for the n rank keys
+  BBTC_TRY(scratch.get(&ka, kcap));
+  BBTC_TRY(scratch.get(&kb, kcap));
+  if (nnz > 0) {
+    k_emit_keys<<<grid_for((nnz + EK_TILE - 1) / EK_TILE, 1, 64), EK_NT, 0, s>>>(
+        d_rowptr, d_colidx, n, nnz, nb, symmetric, sentinel, ka, err);
+    BBTC_LAUNCH_CHECK();
+  }
+  int32_t herr = 0;
+  BBTC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  if (herr & 1) {
+    set_error("bbtc_graph_create: rowptr[0] != 0 or rowptr decreases");
+    return BBTC_EINVAL;
+  }
+  if (herr & 2) {
+    set_error("bbtc_graph_create: colidx entry outside [0, n)");
+    return BBTC_EINVAL;
+  }
+  bool in_alt = false;
+  BBTC_TRY(radix_sort(ka, kb, nullptr, nullptr, nnz, 0, 2 * nb, s, &in_alt));
+  uint64_t *sorted = in_alt ? kb : ka;
+  uint64_t *ukeys = in_alt ? ka : kb;
+
+  BBTC_TRY(dalloc_n(&g->deg, n, s));
+  g->bytes += (uint64_t)(n > 0 ? n : 1) * sizeof(int32_t);
+  BBTC_CUDA(cudaMemsetAsync(g->deg, 0, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s));
+  int64_t m = 0;
+  if (nnz > 0) {
+    const int64_t nblk = (nnz + UQ_TILE - 1) / UQ_TILE;
+    uint64_t *boff = nullptr;
+    BBTC_TRY(scratch.get(&boff, nblk + 1));
+    k_unique_count<<<(unsigned)nblk, UQ_NT, 0, s>>>(sorted, nnz, sentinel, boff);
+    BBTC_LAUNCH_CHECK();
+    BBTC_TRY(exclusive_scan_u64(boff, boff, nblk + 1, s));  // boff[nblk] = total
+    k_unique_write<<<(unsigned)nblk, UQ_NT, 0, s>>>(sorted, nnz, sentinel, boff, nb, ukeys,
+                                                     g->deg);
+    BBTC_LAUNCH_CHECK();
+    BBTC_CUDA(cudaMemcpyAsync(&hstats[0], &boff[nblk], sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  } else {
+    BBTC_CUDA(cudaMemsetAsync(&hstats[0], 0, sizeof(int64_t), s));
+  }
+  int32_t *dmax = nullptr;
+  BBTC_TRY(scratch.get(&dmax, 1));
+  BBTC_TRY(reduce_max_i32(g->deg, n, dmax, s));
+  int64_t stats[2] = {0, 0};
+  int32_t hdmax = 0;
+  BBTC_CUDA(cudaMemcpyAsync(&stats[0], &hstats[0], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaMemcpyAsync(&hdmax, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  m = stats[0];
+  if (m > 0xFFFFFFFFLL) {
+    set_error("bbtc_graph_create: %lld simple edges exceed 2^32 - 1", (long long)m);
+    return BBTC_EINVAL;
+  }
+  g->m = m;
+  g->deg_max = hdmax;
+
+  // ---- a3: order by (degree, id)
+  int32_t *rank = nullptr;
+  BBTC_TRY(scratch.get(&rank, n));
+  BBTC_TRY(dalloc_n(&g->perm, n, s));
+  g->bytes += (uint64_t)(n > 0 ? n : 1) * sizeof(int32_t);
+  // ukeys (m) must survive the rank sort: rank keys go to the sort buffer that
+  // does not hold ukeys, plus a separate alternate buffer.
+  uint64_t *rk = sorted;  // free now (its distinct keys were copied to ukeys)
+  uint64_t *rk_alt = nullptr;
+  BBTC_TRY(scratch.get(&rk_alt, n));
+  if (n > 0) {
+    k_rank_keys<<<grid_for(n, 256, 16), 256, 0, s>>>(g->deg, n, nb, rk);
+    BBTC_LAUNCH_CHECK();
+    int dbits = ceil_log2_u64((uint64_t)hdmax + 1);
+    BBTC_TRY(radix_sort(rk, rk_alt, nullptr, nullptr, n, 0, nb + dbits, s, &in_alt));
+    k_rank_finish<<<grid_for(n, 256, 16), 256, 0, s>>>(in_alt ? rk_alt : rk, n, nb, g->perm,
+                                                        rank);
+    BBTC_LAUNCH_CHECK();
+  }
+
+  // ---- a4: orient and build the oriented CSR
+  BBTC_TRY(dalloc_n(&g->rowptr, n + 1, s));
+  BBTC_TRY(dalloc_n(&g->colidx, m, s));
+  BBTC_TRY(dalloc_n(&g->esrc, m, s));
+  g->bytes += (uint64_t)(n + 1) * 8 + (uint64_t)(m > 0 ? m : 1) * 8;
+  BBTC_CUDA(cudaMemsetAsync(g->rowptr, 0, sizeof(int64_t) * (size_t)(n + 1), s));
+  if (m > 0) {
+    uint64_t *ok = sorted;  // rank keys are consumed; reuse
+    uint64_t *ok_alt = nullptr;
+    BBTC_TRY(scratch.get(&ok_alt, m));
+    k_orient_keys<<<grid_for(m, 256, 32), 256, 0, s>>>(ukeys, m, nb, rank, ok);
+    BBTC_LAUNCH_CHECK();
+    BBTC_TRY(radix_sort(ok, ok_alt, nullptr, nullptr, m, 0, 2 * nb, s, &in_alt));
+    k_csr_finish<<<grid_for(m, 256, 32), 256, 0, s>>>(
+        in_alt ? ok_alt : ok, m, nb, g->colidx, g->esrc,
+        reinterpret_cast<unsigned long long *>(g->rowptr));
+    BBTC_LAUNCH_CHECK();
+  }
+  // rowptr holds the row lengths: their maximum is d+_max, their scan the offsets
+  BBTC_TRY(reduce_max_i64(g->rowptr, n, &hstats[1], s));
+  BBTC_CUDA(cudaMemcpyAsync(&stats[1], &hstats[1], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BBTC_TRY(exclusive_scan_u64(reinterpret_cast<uint64_t *>(g->rowptr),
+                              reinterpret_cast<uint64_t *>(g->rowptr), n + 1, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  g->dplus_max = n > 0 ? stats[1] : 0;
+  return BBTC_OK;
+}
+
+}  // namespace bbtc

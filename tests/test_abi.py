@@ -1,0 +1,67 @@
+"""The C ABI library loads and exports every declared entry point (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2009_12457_gb300 as bb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "bbtc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(bbtc_[a-z_0-9]+)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bbtc_graph_create", "bbtc_count", "bbtc_count_batch",
+                     "bbtc_graph_destroy", "bbtc_last_error", "bbtc_num_tasks"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(bb._build.build())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layout_matches_c():
+    o = bb.bbtc_opts_init()
+    assert o.struct_size == ctypes.sizeof(bb.bbtc_opts)
+    assert o.kernel == 0 and o.p == 0 and o.device_budget_bytes == 0
+
+
+def test_num_tasks():
+    assert [bb.bbtc_num_tasks(p) for p in range(0, 5)] == [0, 1, 4, 10, 20]
+    assert bb.bbtc_num_tasks(36) == 8436
+    assert bb.bbtc_num_tasks(-3) == 0
+
+
+def test_argument_errors_without_touching_the_gpu():
+    lib = bb.load()
+    h = ctypes.c_void_p()
+    rp = np.zeros(2, dtype=np.int64)
+    assert lib.bbtc_graph_create(-1, rp.ctypes.data, None, 0, ctypes.byref(h)) == 1
+    assert "outside" in bb.bbtc_last_error()
+    assert lib.bbtc_graph_create(1, rp.ctypes.data, None, 0, None) == 1
+    assert lib.bbtc_graph_create(1, None, None, 0, ctypes.byref(h)) == 1
+    assert lib.bbtc_graph_create(1, rp.ctypes.data, None, 0x80, ctypes.byref(h)) == 1
+    assert lib.bbtc_graph_create(1 << 31, rp.ctypes.data, None, 0, ctypes.byref(h)) == 1
+    c = ctypes.c_uint64()
+    assert lib.bbtc_count(None, None, ctypes.byref(c)) == 1
+    bad = bb.bbtc_opts_init()
+    bad.struct_size = 8
+    assert lib.bbtc_count_batch(None, -1, ctypes.byref(bad), None, None) == 1
+    lib.bbtc_graph_destroy(None)  # accepted
+
+
+def test_python_binding_rejects_bad_dtypes():
+    with pytest.raises(TypeError):
+        bb.bbtc_graph_create(2, np.zeros(3, dtype=np.int32), np.zeros(0, dtype=np.int32))

@@ -163,3 +163,17 @@ def test_config1_two_oracles_agree():
         assert r5["total"] == T2
     pv = oracle.per_vertex(n, pr["rowptr"], pr["colidx"], pr["perm"])
     assert int(pv.sum()) == 3 * T2
+
+
+def test_vertex_triangles_sampled():
+    rng = np.random.default_rng(21)
+    for _ in range(10):
+        n = int(rng.integers(3, 40))
+        g = pins.with_noise(*G.gnp(n, 0.4, rng), rng)
+        A = G.dense_adjacency(*g)
+        expect = np.rint(np.einsum("ij,ji->i", A @ A, A) / 2).astype(np.int64)
+        for x in range(n):
+            assert oracle.vertex_triangles(*g, x) == expect[x]
+    for k in range(3, 9):
+        for x in range(k):
+            assert oracle.vertex_triangles(*G.complete(k), x) == G.choose(k - 1, 2)
