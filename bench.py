@@ -57,6 +57,8 @@ def make_graph(name: str):
         return graphgen.rmat_s14()
     if name == "chunglu-friendster":
         return graphgen.chunglu_friendster()
+    if name.startswith("rmat-s"):  # smaller/larger instances of the same recipe (profiling)
+        return graphgen.rmat(int(name[6:]), 16, 2)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -132,8 +134,8 @@ def oracle_sample_scale(steps_total: int, budget_s: float = 150.0) -> int:
     """Largest R-MAT scale (same recipe) whose oracle pass fits budget_s / steps."""
     per_step = budget_s / max(steps_total, 1)
     scale = 12
-    for s in range(12, 20):
-        if 8.0 * 2.3 ** (s - 18) <= per_step:  # measured: ~6-8 s at scale 18
+    for s in range(12, 21):
+        if 6.0 * 2.3 ** (s - 19) <= per_step:  # measured on the GPU host: 5.8 s at scale 19
             scale = s
     return scale
 
@@ -150,8 +152,7 @@ def run_oracle_sample(scale: int, p: int):
 
 
 def cpu_baseline(steps_total: int, p: int):
-    scale = oracle_sample_scale(steps_total, budget_s=30.0 * steps_total)
-    scale = min(scale, 19)
+    scale = oracle_sample_scale(steps_total, budget_s=20.0 * steps_total)
     m, dt, total = run_oracle_sample(scale, p)
     return {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"oracle pipeline (canonicalise, order, orient, partition p={p}, "
@@ -178,7 +179,7 @@ def reference_arm(args, rank: int, world: int):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "p": p,
+        "config": {"workload": WORKLOADS.get(args.workload, args.workload), "p": p,
                    "sample": f"R-MAT scale {scale}, edge factor 16, seed 2 ({m} edges)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"R-MAT scale {scale}, edge factor 16, seed 2 per step"},
@@ -195,7 +196,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat-s23", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat-s23",
+                    help="rmat-s23 (default), rmat-s14, chunglu-friendster, or rmat-sNN")
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--kernel", default="auto", choices=["auto", "intersect", "hashmap"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -322,7 +324,8 @@ def main():
             "dtype": "int32",
             "data": "synthetic",
             "config": {
-                "workload": WORKLOADS[args.workload], "p": p, "kernel": args.kernel,
+                "workload": WORKLOADS.get(args.workload, args.workload), "p": p,
+                "kernel": args.kernel,
                 "n": n, "m": m, "triangles": next(iter(totals)),
                 "input_entries": int(h_ci.numel()),
                 "l2": "inputs larger than L2 (input CSR %.2f GB, oriented CSR %.2f GB)"

@@ -45,15 +45,54 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Per-warp shared staging area for N(G_jk, v) (int32 slots).
+constexpr int STAGE = 2048;
+constexpr int MIN_STAGE = 8;
+constexpr int32_t EMPTY = -1;
+
+__device__ __forceinline__ uint32_t hash_slot(int32_t w, int log2h) {
+  return ((uint32_t)w * 2654435761u) >> (32 - log2h);
+}
+
+// Membership of w in the sorted list stage[0, len).
+__device__ __forceinline__ bool sorted_contains(const int32_t *stage, int len, int32_t w) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (stage[mid] < w) lo = mid + 1; else hi = mid;
+  }
+  return lo < len && stage[lo] == w;
+}
+
+// Membership of w in the open-addressed table stage[0, 2^log2h) (linear probing;
+// the table is at most half full, so an empty slot ends every probe sequence).
+__device__ __forceinline__ bool hash_contains(const int32_t *stage, int log2h, int32_t w) {
+  const uint32_t mask = (1u << log2h) - 1u;
+  uint32_t h = hash_slot(w, log2h);
+  for (uint32_t n = 0; n <= mask; ++n) {
+    const int32_t s = stage[h];
+    if (s == w) return true;
+    if (s == EMPTY) return false;
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+
 template <bool PER_VERTEX>
 __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
+  extern __shared__ int32_t count_smem[];
   __shared__ int32_t cuts[MAXP + 1];
   for (int i = threadIdx.x; i <= P.p; i += CT_NT) cuts[i] = P.cuts[i];
   __syncthreads();
   const unsigned lane = threadIdx.x & 31u;
+  int32_t *stage = count_smem + (threadIdx.x >> 5) * STAGE;
   const uint64_t t_start = P.timeout_ns ? global_ns() : 0;
   const int64_t *__restrict__ rowptr = P.rowptr;
   const int32_t *__restrict__ col = P.colidx;
+  // (task, v) whose N(G_jk, v) is in `stage`, and how it is stored
+  unsigned long long staged_tag = ~0ull;
+  int staged_len = 0, staged_log2h = 0;
+  bool staged_hash = false;
 
   for (;;) {
     unsigned long long it = 0;
@@ -66,32 +105,90 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
     }
     const WorkItem w = P.items[it];
     const int t = w.task;
+    const bool use_hash = (w.flags & 1) != 0;
     const int j = P.tasks[3 * t + 1], k = P.tasks[3 * t + 2];
     const int32_t ck = cuts[k], ck1 = cuts[k + 1];
     unsigned long long acc = 0;
 
     for (int64_t base = w.x0; base < w.x1; base += 32) {
       const int64_t x = base + lane;
-      int64_t s0 = 0, s1 = 0, b0 = 0, b1 = 0;
-      int32_t u = 0, v = 0;
-      if (x < w.x1) {
+      const bool valid = x < w.x1;
+      int32_t u = 0, v = -1;
+      int64_t e = 0;
+      if (valid) {
         u = P.ie_u[x];
         v = P.ie_v[x];
-        const int64_t e = P.ie_e[x];
-        const int64_t ru1 = rowptr[u + 1];
-        // N(G_ik, u) restricted to entries above v
-        s0 = (k == j) ? e + 1 : lower_bound_dev<int32_t, int64_t>(col, rowptr[u], ru1, ck);
-        s1 = lower_bound_dev<int32_t, int64_t>(col, s0, ru1, ck1);
-        // N(G_jk, v)
+        e = P.ie_e[x];
+      }
+      // in-edges are sorted by destination: a batch whose first and last
+      // valid entries agree shares one v (and one list N(G_jk, v))
+      const int32_t v0 = __shfl_sync(0xffffffffu, v, 0);
+      const bool uniform = __all_sync(0xffffffffu, !valid || v == v0);
+      int64_t b0 = 0, b1 = 0;
+      if (uniform) {
+        if (lane == 0) {
+          const int64_t rv1 = rowptr[v0 + 1];
+          b0 = lower_bound_dev<int32_t, int64_t>(col, rowptr[v0], rv1, ck);
+          b1 = lower_bound_dev<int32_t, int64_t>(col, b0, rv1, ck1);
+        }
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        b1 = __shfl_sync(0xffffffffu, b1, 0);
+      } else if (valid) {
         const int64_t rv1 = rowptr[v + 1];
         b0 = lower_bound_dev<int32_t, int64_t>(col, rowptr[v], rv1, ck);
         b1 = lower_bound_dev<int32_t, int64_t>(col, b0, rv1, ck1);
-        if (b1 == b0) s1 = s0;
+      }
+      // N(G_ik, u) restricted to entries above v
+      int64_t s0 = 0, s1 = 0;
+      if (valid && b1 > b0) {
+        const int64_t ru1 = rowptr[u + 1];
+        s0 = (k == j) ? e + 1 : lower_bound_dev<int32_t, int64_t>(col, rowptr[u], ru1, ck);
+        s1 = lower_bound_dev<int32_t, int64_t>(col, s0, ru1, ck1);
       }
       const uint32_t len = (uint32_t)(s1 - s0);
       const uint32_t incl = warp_inclusive_scan(len);
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total == 0) continue;
       const uint32_t excl = incl - len;
+
+      // stage N(G_jk, v) once per (task, v) segment: sorted copy for
+      // bbTC-Intersect, hash table for bbTC-HMap
+      const int blen = (int)(b1 - b0);
+      bool staged = false;
+      if (uniform && blen >= MIN_STAGE && blen <= STAGE) {
+        const bool want_hash = use_hash && blen <= STAGE / 2;
+        const unsigned long long tag =
+            ((unsigned long long)(uint32_t)t << 33) | ((unsigned long long)(uint32_t)v0 << 1) |
+            (want_hash ? 1ull : 0ull);
+        if (tag != staged_tag) {
+          __syncwarp();
+          if (want_hash) {
+            int log2h = 5;
+            while ((1 << log2h) < 2 * blen) ++log2h;
+            const int hsize = 1 << log2h;
+            for (int i = lane; i < hsize; i += 32) stage[i] = EMPTY;
+            __syncwarp();
+            const uint32_t hmask = (uint32_t)hsize - 1u;
+            for (int i = lane; i < blen; i += 32) {
+              const int32_t key = col[b0 + i];
+              uint32_t h = hash_slot(key, log2h);
+              for (int n = 0; n < hsize; ++n) {
+                if (atomicCAS(&stage[h], EMPTY, key) == EMPTY) break;
+                h = (h + 1) & hmask;
+              }
+            }
+            staged_log2h = log2h;
+          } else {
+            for (int i = lane; i < blen; i += 32) stage[i] = col[b0 + i];
+          }
+          __syncwarp();
+          staged_tag = tag;
+          staged_len = blen;
+          staged_hash = want_hash;
+        }
+        staged = true;
+      }
+
       for (uint32_t q0 = 0; q0 < total; q0 += 32) {
         const uint32_t q = q0 + lane;
         // owner: the last lane whose exclusive prefix is <= q
@@ -102,9 +199,12 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
           if (ex <= q) o += step;
         }
         const int64_t so = __shfl_sync(0xffffffffu, s0, o);
-        const int64_t bo0 = __shfl_sync(0xffffffffu, b0, o);
-        const int64_t bo1 = __shfl_sync(0xffffffffu, b1, o);
         const uint32_t exo = __shfl_sync(0xffffffffu, excl, o);
+        int64_t bo0 = b0, bo1 = b1;
+        if (!uniform) {
+          bo0 = __shfl_sync(0xffffffffu, b0, o);
+          bo1 = __shfl_sync(0xffffffffu, b1, o);
+        }
         int32_t uo = 0, vo = 0;
         if (PER_VERTEX) {
           uo = __shfl_sync(0xffffffffu, u, o);
@@ -112,8 +212,15 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
         }
         if (q < total) {
           const int32_t wv = col[so + (q - exo)];
-          const int64_t pos = lower_bound_dev<int32_t, int64_t>(col, bo0, bo1, wv);
-          if (pos < bo1 && col[pos] == wv) {
+          bool hit;
+          if (staged) {
+            hit = staged_hash ? hash_contains(stage, staged_log2h, wv)
+                              : sorted_contains(stage, staged_len, wv);
+          } else {
+            const int64_t pos = lower_bound_dev<int32_t, int64_t>(col, bo0, bo1, wv);
+            hit = pos < bo1 && col[pos] == wv;
+          }
+          if (hit) {
             ++acc;
             if (PER_VERTEX) {
               atomicAdd(&P.vcount[uo], 1ull);
@@ -216,14 +323,20 @@ bbtc_status run_count(bbtc_graph *g, const Plan &pl, const CountOutputs &out,
     P.status = out.status;
     P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
     const bool pv = out.vertex_count != nullptr;
+    const size_t smem = (size_t)(CT_NT / 32) * STAGE * sizeof(int32_t);
     int &blocks_per_sm = g_count_blocks[pv];
     if (!blocks_per_sm) {
-      if (pv)
+      if (pv) {
+        BBTC_CUDA(cudaFuncSetAttribute(k_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
         BBTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_count<true>,
-                                                                CT_NT, 0));
-      else
+                                                                CT_NT, smem));
+      } else {
+        BBTC_CUDA(cudaFuncSetAttribute(k_count<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         BBTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_count<false>,
-                                                                CT_NT, 0));
+                                                                CT_NT, smem));
+      }
       if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     int64_t blocks = (int64_t)num_sms() * blocks_per_sm;
@@ -231,9 +344,9 @@ bbtc_status run_count(bbtc_graph *g, const Plan &pl, const CountOutputs &out,
     if (blocks > need) blocks = need;
     if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
     if (pv)
-      k_count<true><<<(unsigned)blocks, CT_NT, 0, s>>>(P);
+      k_count<true><<<(unsigned)blocks, CT_NT, smem, s>>>(P);
     else
-      k_count<false><<<(unsigned)blocks, CT_NT, 0, s>>>(P);
+      k_count<false><<<(unsigned)blocks, CT_NT, smem, s>>>(P);
     BBTC_LAUNCH_CHECK();
     if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
   } else {
