@@ -78,17 +78,34 @@ __device__ __forceinline__ bool hash_contains(const int32_t *stage, int log2h, i
   return false;
 }
 
+// Per-batch lane records, shared by the warp: where each in-edge's probes
+// start in the flattened probe sequence and where they come from.
+struct LaneRec {
+  int64_t s0[32];    // first probe element (index into colidx) of each lane's in-edge
+  int64_t b0[32];    // N(G_jk, v) range of each lane (mixed batches only)
+  int64_t b1[32];
+  uint32_t incl[32];  // inclusive prefix of the probe counts
+  int32_t u[32];
+  int32_t v[32];
+};
+
+constexpr int UNIFORM_MIN = 4;  // a run of >= 4 in-edges into one v is a uniform batch
+
 template <bool PER_VERTEX>
 __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
-  extern __shared__ int32_t count_smem[];
+  extern __shared__ __align__(16) unsigned char count_smem_raw[];
   __shared__ int32_t cuts[MAXP + 1];
   for (int i = threadIdx.x; i <= P.p; i += CT_NT) cuts[i] = P.cuts[i];
   __syncthreads();
   const unsigned lane = threadIdx.x & 31u;
-  int32_t *stage = count_smem + (threadIdx.x >> 5) * STAGE;
+  const int warp = threadIdx.x >> 5;
+  int32_t *stage = reinterpret_cast<int32_t *>(count_smem_raw) + warp * STAGE;
+  LaneRec &rec = reinterpret_cast<LaneRec *>(count_smem_raw + (size_t)(CT_NT / 32) * STAGE *
+                                                                  sizeof(int32_t))[warp];
   const uint64_t t_start = P.timeout_ns ? global_ns() : 0;
   const int64_t *__restrict__ rowptr = P.rowptr;
   const int32_t *__restrict__ col = P.colidx;
+  const unsigned lt_mask = (1u << lane) - 1u;
   // (task, v) whose N(G_jk, v) is in `stage`, and how it is stored
   unsigned long long staged_tag = ~0ull;
   int staged_len = 0, staged_log2h = 0;
@@ -108,51 +125,69 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
     const bool use_hash = (w.flags & 1) != 0;
     const int j = P.tasks[3 * t + 1], k = P.tasks[3 * t + 2];
     const int32_t ck = cuts[k], ck1 = cuts[k + 1];
+    const bool diag = k == j;          // N(G_jk, v) starts at N(v)'s start
+    const bool last = k == P.p - 1;    // partial lists run to the row's end
     unsigned long long acc = 0;
 
-    for (int64_t base = w.x0; base < w.x1; base += 32) {
+    int64_t base = w.x0;
+    while (base < w.x1) {
       const int64_t x = base + lane;
       const bool valid = x < w.x1;
-      int32_t u = 0, v = -1;
+      const int32_t v = valid ? P.ie_v[x] : -1;
+      // in-edges are sorted by destination: lanes equal to lane 0's v form a prefix
+      const int32_t v0 = __shfl_sync(0xffffffffu, v, 0);
+      const unsigned eq = __ballot_sync(0xffffffffu, valid && v == v0);
+      const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+      const int run0 = __popc(eq);
+      const int nvalid = __popc(vmask);
+      const bool uniform = run0 >= UNIFORM_MIN || run0 == nvalid;
+      int nb;  // in-edges handled by this batch
+      if (uniform) {
+        nb = run0;
+      } else {
+        // cut before the last run, which may continue past the batch
+        const int32_t vprev = __shfl_up_sync(0xffffffffu, v, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, valid && (lane == 0 || v != vprev));
+        const int last_head = 31 - __clz(heads);
+        nb = (base + 32 < w.x1 && last_head > 0) ? last_head : nvalid;
+      }
+      base += nb;
+      const bool active = (int)lane < nb;
+
+      int32_t u = 0;
       int64_t e = 0;
-      if (valid) {
+      if (active) {
         u = P.ie_u[x];
-        v = P.ie_v[x];
         e = P.ie_e[x];
       }
-      // in-edges are sorted by destination: a batch whose first and last
-      // valid entries agree shares one v (and one list N(G_jk, v))
-      const int32_t v0 = __shfl_sync(0xffffffffu, v, 0);
-      const bool uniform = __all_sync(0xffffffffu, !valid || v == v0);
       int64_t b0 = 0, b1 = 0;
       if (uniform) {
         if (lane == 0) {
-          const int64_t rv1 = rowptr[v0 + 1];
-          b0 = lower_bound_dev<int32_t, int64_t>(col, rowptr[v0], rv1, ck);
-          b1 = lower_bound_dev<int32_t, int64_t>(col, b0, rv1, ck1);
+          const int64_t rv0 = rowptr[v0], rv1 = rowptr[v0 + 1];
+          b0 = diag ? rv0 : lower_bound_dev<int32_t, int64_t>(col, rv0, rv1, ck);
+          b1 = last ? rv1 : lower_bound_dev<int32_t, int64_t>(col, b0, rv1, ck1);
         }
         b0 = __shfl_sync(0xffffffffu, b0, 0);
         b1 = __shfl_sync(0xffffffffu, b1, 0);
-      } else if (valid) {
-        const int64_t rv1 = rowptr[v + 1];
-        b0 = lower_bound_dev<int32_t, int64_t>(col, rowptr[v], rv1, ck);
-        b1 = lower_bound_dev<int32_t, int64_t>(col, b0, rv1, ck1);
+      } else if (active) {
+        const int64_t rv0 = rowptr[v], rv1 = rowptr[v + 1];
+        b0 = diag ? rv0 : lower_bound_dev<int32_t, int64_t>(col, rv0, rv1, ck);
+        b1 = last ? rv1 : lower_bound_dev<int32_t, int64_t>(col, b0, rv1, ck1);
       }
       // N(G_ik, u) restricted to entries above v
       int64_t s0 = 0, s1 = 0;
-      if (valid && b1 > b0) {
+      if (active && b1 > b0) {
         const int64_t ru1 = rowptr[u + 1];
-        s0 = (k == j) ? e + 1 : lower_bound_dev<int32_t, int64_t>(col, rowptr[u], ru1, ck);
-        s1 = lower_bound_dev<int32_t, int64_t>(col, s0, ru1, ck1);
+        s0 = diag ? e + 1 : lower_bound_dev<int32_t, int64_t>(col, rowptr[u], ru1, ck);
+        s1 = last ? ru1 : lower_bound_dev<int32_t, int64_t>(col, s0, ru1, ck1);
       }
       const uint32_t len = (uint32_t)(s1 - s0);
       const uint32_t incl = warp_inclusive_scan(len);
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
       if (total == 0) continue;
-      const uint32_t excl = incl - len;
 
-      // stage N(G_jk, v) once per (task, v) segment: sorted copy for
-      // bbTC-Intersect, hash table for bbTC-HMap
+      // stage N(G_jk, v) once per (task, v): sorted copy (bbTC-Intersect) or
+      // hash table (bbTC-HMap)
       const int blen = (int)(b1 - b0);
       bool staged = false;
       if (uniform && blen >= MIN_STAGE && blen <= STAGE) {
@@ -160,7 +195,9 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
         const unsigned long long tag =
             ((unsigned long long)(uint32_t)t << 33) | ((unsigned long long)(uint32_t)v0 << 1) |
             (want_hash ? 1ull : 0ull);
-        if (tag != staged_tag) {
+        if (tag == staged_tag) {
+          staged = true;
+        } else if (nb == 32 || total >= (uint32_t)blen / 2) {
           __syncwarp();
           if (want_hash) {
             int log2h = 5;
@@ -185,51 +222,70 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
           staged_tag = tag;
           staged_len = blen;
           staged_hash = want_hash;
+          staged = true;
         }
-        staged = true;
       }
 
-      for (uint32_t q0 = 0; q0 < total; q0 += 32) {
-        const uint32_t q = q0 + lane;
-        // owner: the last lane whose exclusive prefix is <= q
+      // each lane walks a contiguous run of the flattened probes
+      rec.s0[lane] = s0;
+      rec.incl[lane] = incl;
+      if (!uniform) {
+        rec.b0[lane] = b0;
+        rec.b1[lane] = b1;
+      }
+      if (PER_VERTEX) {
+        rec.u[lane] = u;
+        rec.v[lane] = uniform ? v0 : v;
+      }
+      __syncwarp();
+      const uint32_t per = (total + 31) >> 5;
+      const uint32_t qa = lane * per;
+      const uint32_t qb = qa + per < total ? qa + per : total;
+      if (qa < qb) {
+        // owner of qa: the first lane whose inclusive prefix exceeds qa
         int o = 0;
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          uint32_t ex = __shfl_sync(0xffffffffu, excl, o + step);
-          if (ex <= q) o += step;
-        }
-        const int64_t so = __shfl_sync(0xffffffffu, s0, o);
-        const uint32_t exo = __shfl_sync(0xffffffffu, excl, o);
-        int64_t bo0 = b0, bo1 = b1;
+        for (int step = 16; step > 0; step >>= 1)
+          if (rec.incl[o + step - 1] <= qa) o += step;
+        uint32_t o_end = rec.incl[o];
+        // addr + q indexes colidx for every q owned by o
+        int64_t addr = rec.s0[o] - (int64_t)(o == 0 ? 0 : rec.incl[o - 1]);
+        int64_t lo = b0, hi = b1;
         if (!uniform) {
-          bo0 = __shfl_sync(0xffffffffu, b0, o);
-          bo1 = __shfl_sync(0xffffffffu, b1, o);
+          lo = rec.b0[o];
+          hi = rec.b1[o];
         }
-        int32_t uo = 0, vo = 0;
-        if (PER_VERTEX) {
-          uo = __shfl_sync(0xffffffffu, u, o);
-          vo = __shfl_sync(0xffffffffu, v, o);
-        }
-        if (q < total) {
-          const int32_t wv = col[so + (q - exo)];
+        for (uint32_t q = qa; q < qb; ++q) {
+          while (q >= o_end) {
+            ++o;
+            const uint32_t prev_end = o_end;
+            o_end = rec.incl[o];
+            addr = rec.s0[o] - (int64_t)prev_end;
+            if (!uniform) {
+              lo = rec.b0[o];
+              hi = rec.b1[o];
+            }
+          }
+          const int32_t wv = col[addr + q];
           bool hit;
           if (staged) {
             hit = staged_hash ? hash_contains(stage, staged_log2h, wv)
                               : sorted_contains(stage, staged_len, wv);
           } else {
-            const int64_t pos = lower_bound_dev<int32_t, int64_t>(col, bo0, bo1, wv);
-            hit = pos < bo1 && col[pos] == wv;
+            const int64_t pos = lower_bound_dev<int32_t, int64_t>(col, lo, hi, wv);
+            hit = pos < hi && col[pos] == wv;
           }
           if (hit) {
             ++acc;
             if (PER_VERTEX) {
-              atomicAdd(&P.vcount[uo], 1ull);
-              atomicAdd(&P.vcount[vo], 1ull);
+              atomicAdd(&P.vcount[rec.u[o]], 1ull);
+              atomicAdd(&P.vcount[rec.v[o]], 1ull);
               atomicAdd(&P.vcount[wv], 1ull);
             }
           }
         }
       }
+      __syncwarp();
     }
     acc = warp_sum(acc);
     if (lane == 0 && acc) atomicAdd(&P.task_count[t], acc);
@@ -268,6 +324,10 @@ __global__ void k_wedges(const int64_t *__restrict__ rowptr, const int32_t *__re
 }
 
 int g_count_blocks[2] = {0, 0};
+
+size_t count_smem_bytes() {
+  return (size_t)(CT_NT / 32) * (STAGE * sizeof(int32_t) + sizeof(LaneRec));
+}
 
 }  // namespace
 
@@ -323,7 +383,7 @@ bbtc_status run_count(bbtc_graph *g, const Plan &pl, const CountOutputs &out,
     P.status = out.status;
     P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
     const bool pv = out.vertex_count != nullptr;
-    const size_t smem = (size_t)(CT_NT / 32) * STAGE * sizeof(int32_t);
+    const size_t smem = count_smem_bytes();
     int &blocks_per_sm = g_count_blocks[pv];
     if (!blocks_per_sm) {
       if (pv) {
