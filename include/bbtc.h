@@ -133,6 +133,39 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts, uint64_t *count);
 bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts *opts,
                              uint64_t *counts, bbtc_status *per_graph);
 
+/*
+ * Allocation-free count. The paper has no counterpart to this entry point: it
+ * exists for callers that cannot allocate device memory at the moment they
+ * count. Examples are a serving loop that reserves all of its GPU memory at
+ * start-up and forbids later allocations, code running while another memory
+ * manager (a framework's caching allocator) owns the free device memory, and
+ * hooks invoked from inside an allocator, where cudaMalloc would re-enter it.
+ *
+ * It runs the same counting kernel as bbtc_count on the plan that an earlier
+ * bbtc_count or bbtc_graph_get_plan call built for the same p on this handle.
+ * Its scratch (work-stealing counter, status, per-task accumulators) is a
+ * fixed 8 KiB device array inside the library, which every GPU that loads the
+ * library holds until the process exits. The call makes no cudaMalloc,
+ * cudaMallocAsync, cudaFree or other allocating call.
+ *
+ *   p             1..16: the fixed array holds at most 816 task counters
+ *   count_dev     DEVICE pointer to one uint64: the total
+ *   per_task_dev  NULL, or DEVICE pointer to bbtc_num_tasks(p) uint64 in Alg. 4 order
+ *   stream        cudaStream_t (NULL = the handle's stream); the call is
+ *                 asynchronous: outputs are ready when the stream reaches them
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Every call shares the one array and it keeps the last call's
+ * contents: each call clears what it needs, but calls whose work overlaps on
+ * the GPU (other streams, other host threads) race on it and must be ordered
+ * by the caller.
+ * Errors: EINVAL for a NULL handle or count_dev, p outside 1..16, or no plan
+ * for p on the handle; ECUDA.
+ */
+bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *count_dev,
+                               uint64_t *per_task_dev, void *stream);
+
 /* Free the handle and its device memory. Accepts NULL. */
 void bbtc_graph_destroy(bbtc_graph_t g);
 

@@ -22,7 +22,7 @@ __all__ = [
     "BbtcError", "Graph", "bbtc_graph_create", "bbtc_graph_create_async", "bbtc_count",
     "bbtc_count_batch", "bbtc_graph_destroy", "bbtc_last_error", "bbtc_num_tasks",
     "bbtc_opts_init", "bbtc_graph_get_info", "bbtc_graph_get_oriented", "bbtc_graph_get_plan",
-    "bbtc_graph_get_timings", "bbtc_kernel_launches",
+    "bbtc_graph_get_timings", "bbtc_kernel_launches", "bbtc_count_noalloc",
     "library_path", "load",
 ]
 
@@ -122,6 +122,8 @@ def load():
         lib.bbtc_graph_get_timings.restype = st
         lib.bbtc_kernel_launches.argtypes = []
         lib.bbtc_kernel_launches.restype = u64
+        lib.bbtc_count_noalloc.argtypes = [P, i32, P, P, P]
+        lib.bbtc_count_noalloc.restype = st
         _lib = lib
         return lib
 
@@ -219,6 +221,15 @@ def bbtc_count(handle: int, opts: bbtc_opts | None = None) -> int:
     _check(load().bbtc_count(handle, ctypes.byref(opts) if opts is not None else None,
                              ctypes.byref(c)))
     return int(c.value)
+
+
+def bbtc_count_noalloc(handle: int, p: int, count_dev, per_task_dev=None, stream=None) -> None:
+    """Allocation-free count into device buffers (see include/bbtc.h)."""
+    c, c_dev = _ptr(count_dev)
+    t, t_dev = _ptr(per_task_dev)
+    if not c_dev or (per_task_dev is not None and not t_dev):
+        raise ValueError("bbtc_count_noalloc writes device buffers only")
+    _check(load().bbtc_count_noalloc(handle, p, c, t or None, _stream_ptr(stream) or None))
 
 
 def bbtc_count_batch(handles, opts: bbtc_opts | None = None):

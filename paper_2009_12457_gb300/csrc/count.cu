@@ -419,3 +419,131 @@ bbtc_status run_count(bbtc_graph *g, const Plan &pl, const CountOutputs &out,
 }
 
 }  // namespace bbtc
+
+// ------------------------------------------------ allocation-free counting
+//
+// bbtc_count_noalloc runs the same counting kernel as bbtc_count, but keeps its
+// scratch (the work-stealing counter, the status word and the per-task
+// accumulators) in the fixed device array below instead of allocating it.
+// The array is 8 KiB; every GPU that loads the library holds it until exit.
+
+namespace bbtc {
+namespace {
+
+constexpr int NOALLOC_MAX_P = 16;                  // p(p+1)(p+2)/6 = 816 tasks
+constexpr int NOALLOC_WORDS = 1024;                // 8 KiB of uint64
+constexpr int NOALLOC_HEAD = 0, NOALLOC_STATUS = 1, NOALLOC_TASKS = 2;
+static_assert(NOALLOC_TASKS + NOALLOC_MAX_P * (NOALLOC_MAX_P + 1) * (NOALLOC_MAX_P + 2) / 6 <=
+                  NOALLOC_WORDS,
+              "no-alloc scratch too small for NOALLOC_MAX_P");
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_WORDS];
+
+// Device address of g_noalloc_scratch on each device (the host-side symbol is
+// only a stand-in and must never be handed to a kernel).
+unsigned long long *g_noalloc_addr[64] = {nullptr};
+
+bbtc_status noalloc_scratch(unsigned long long **out) {
+  int dev = 0;
+  BBTC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("bbtc_count_noalloc: device ordinal %d out of range", dev);
+    return BBTC_EINVAL;
+  }
+  if (!g_noalloc_addr[dev]) {
+    void *ptr = nullptr;
+    BBTC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_addr[dev] = static_cast<unsigned long long *>(ptr);
+  }
+  *out = g_noalloc_addr[dev];
+  return BBTC_OK;
+}
+
+}  // namespace
+}  // namespace bbtc
+
+extern "C" bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *count_dev,
+                                          uint64_t *per_task_dev, void *stream) {
+  using namespace bbtc;
+  clear_error();
+  if (!g || !count_dev) {
+    set_error("bbtc_count_noalloc: NULL handle or count_dev");
+    return BBTC_EINVAL;
+  }
+  if (p < 1 || p > NOALLOC_MAX_P) {
+    set_error("bbtc_count_noalloc: p = %d is outside 1..%d (fixed scratch holds %d tasks)", p,
+              NOALLOC_MAX_P, NOALLOC_WORDS - NOALLOC_TASKS);
+    return BBTC_EINVAL;
+  }
+  const Plan &pl = g->plan;
+  if (pl.p != p) {
+    set_error("bbtc_count_noalloc: no plan for p = %d on this handle; call bbtc_count or "
+              "bbtc_graph_get_plan with that p first", p);
+    return BBTC_EINVAL;
+  }
+  int prev = -1;
+  if (cudaGetDevice(&prev) == cudaSuccess && prev != g->device) cudaSetDevice(g->device);
+  else prev = -1;
+  cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
+  bbtc_status st = BBTC_OK;
+  do {
+    unsigned long long *scratch = nullptr;
+    if ((st = noalloc_scratch(&scratch)) != BBTC_OK) break;
+    unsigned long long *task_count = scratch + NOALLOC_TASKS;
+    const int64_t nt = pl.ntasks;
+    // the array keeps the previous call's contents: clear what must start at 0
+    if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (size_t)(NOALLOC_TASKS + nt),
+                        s) != cudaSuccess ||
+        cudaMemsetAsync(count_dev, 0, sizeof(uint64_t), s) != cudaSuccess) {
+      set_error("bbtc_count_noalloc: cudaMemsetAsync failed");
+      st = BBTC_ECUDA;
+      break;
+    }
+    if (pl.nitems > 0) {
+      CountParams P;
+      P.rowptr = g->rowptr;
+      P.colidx = g->colidx;
+      P.ie_u = pl.ie_u;
+      P.ie_v = pl.ie_v;
+      P.ie_e = pl.ie_e;
+      P.cuts = pl.cuts;
+      P.p = pl.p;
+      P.tasks = pl.tasks;
+      P.items = pl.items;
+      P.nitems = pl.nitems;
+      P.head = scratch + NOALLOC_HEAD;
+      P.task_count = task_count;
+      P.vcount = nullptr;
+      P.status = reinterpret_cast<int32_t *>(scratch + NOALLOC_STATUS);
+      P.timeout_ns = 0;
+      const size_t smem = count_smem_bytes();
+      int blocks_per_sm = 0;
+      if (cudaFuncSetAttribute(k_count<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_count<false>, CT_NT,
+                                                        smem) != cudaSuccess) {
+        set_error("bbtc_count_noalloc: kernel configuration failed");
+        st = BBTC_ECUDA;
+        break;
+      }
+      if (blocks_per_sm < 1) blocks_per_sm = 1;
+      int64_t blocks = (int64_t)num_sms() * blocks_per_sm;
+      const int64_t need = (pl.nitems + CT_NT / 32 - 1) / (CT_NT / 32);
+      if (blocks > need) blocks = need;
+      k_count<false><<<(unsigned)blocks, CT_NT, smem, s>>>(P);
+      if ((st = launch_status("bbtc_count_noalloc")) != BBTC_OK) break;
+    }
+    k_sum_u64<<<grid_for(nt, 256, 2), 256, 0, s>>>(
+        task_count, nt, reinterpret_cast<unsigned long long *>(count_dev));
+    if ((st = launch_status("bbtc_count_noalloc")) != BBTC_OK) break;
+    if (per_task_dev &&
+        cudaMemcpyAsync(per_task_dev, task_count, sizeof(uint64_t) * (size_t)nt,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      set_error("bbtc_count_noalloc: cudaMemcpyAsync failed");
+      st = BBTC_ECUDA;
+      break;
+    }
+  } while (0);
+  if (prev >= 0) cudaSetDevice(prev);
+  return st;
+}
