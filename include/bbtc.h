@@ -71,6 +71,10 @@ typedef struct {
   uint32_t flags;               /* BBTC_OUT_DEVICE: the two output arrays are device pointers */
   int32_t hash_threshold;       /* AUTO: tasks whose mean staged list exceeds this use HMap;
                                    0 = built-in default */
+  uint64_t *per_graph_out;      /* NULL, or one uint64 per graph of a batch handle
+                                   (bbtc_graph_create_batch / bbtc_count_batch) */
+  int32_t chunk;                /* in-edges per work item of the counting kernel; 0 = auto */
+  int32_t reserved;             /* must be 0 */
 } bbtc_opts;
 
 #define BBTC_OUT_DEVICE 0x1u
@@ -108,6 +112,29 @@ bbtc_status bbtc_graph_create_async(int64_t n, const int64_t *rowptr, const int3
                                     uint32_t flags, void *stream, bbtc_graph_t *out);
 
 /*
+ * One handle for a batch of ng independent graphs, prepared together as their
+ * disjoint union (one canonicalisation, order and orientation pass). Graph g
+ * owns the union's vertices [vertex_offsets[g], vertex_offsets[g+1]). Within
+ * a graph the degree order and the orientation are the same as for the graph
+ * alone (ties by id keep each graph's own order), no triangle spans two
+ * graphs, and bbtc_count with opts.per_graph_out returns every graph's exact
+ * count from one counting launch over the union.
+ *
+ *   ng              number of graphs, >= 1
+ *   vertex_offsets  ng+1 HOST int64: 0 = offsets[0] <= ... <= offsets[ng] = N
+ *   rowptr          N+1 int64 offsets of the union's rows (host, or device
+ *                   with BBTC_INPUT_DEVICE)
+ *   colidx          rowptr[N] int32 neighbour ids LOCAL to the row's graph:
+ *                   an entry of a row of graph g lies in [0, n_g)
+ *
+ * Errors: as bbtc_graph_create, plus EINVAL for decreasing offsets or an
+ * entry outside its graph.
+ */
+bbtc_status bbtc_graph_create_batch(int32_t ng, const int64_t *vertex_offsets,
+                                    const int64_t *rowptr, const int32_t *colidx, uint32_t flags,
+                                    void *stream, bbtc_graph_t *out);
+
+/*
  * Count the triangles of the handle's graph with bbTC at p x p blocks:
  * contiguous symmetric partition of the degree order balanced on oriented
  * edges, tasks (i,j,k), i <= j <= k (Alg. 4), ordered by the Sec. 5 estimate
@@ -124,11 +151,15 @@ bbtc_status bbtc_graph_create_async(int64_t n, const int64_t *rowptr, const int3
 bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts, uint64_t *count);
 
 /*
- * Count ng independent graphs in one persistent launch. counts receives ng
- * uint64 totals; per_graph (nullable) receives each graph's status. Options
- * other than p, kernel and stream apply to none of the graphs (per-task and
- * per-vertex outputs are not produced in batch mode). p = 0 picks p per graph.
- * Errors: EINVAL for ng < 0 or a NULL handle; the first failing graph's status.
+ * Count ng independent handles in one persistent launch: their oriented
+ * CSRs are gathered on the device into one union (positions offset per
+ * handle), planned once and counted by one kernel launch whose hits are
+ * attributed to their graph. counts receives ng uint64 totals; per_graph
+ * (nullable) receives each graph's status. Options other than p, kernel,
+ * hash_threshold, chunk and stream are ignored (no per-task, per-vertex or
+ * per-graph outputs). p = 0 picks p from the union's size.
+ * Errors: EINVAL for ng < 0 or a NULL handle (its status is EINVAL and the
+ * others are still counted); ENOMEM; ECUDA.
  */
 bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts *opts,
                              uint64_t *counts, bbtc_status *per_graph);
@@ -166,6 +197,21 @@ bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts
 bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *count_dev,
                                uint64_t *per_task_dev, void *stream);
 
+/*
+ * Enqueue a count on opts->stream (NULL = the handle's stream) without
+ * allocating and without waiting: the plan for (p, kernel, hash_threshold,
+ * chunk) must already exist on the handle (built by bbtc_count or
+ * bbtc_graph_get_plan), and every output is a DEVICE pointer: total_dev (one
+ * uint64), opts->per_task_out and opts->per_graph_out (nullable;
+ * opts->flags must include BBTC_OUT_DEVICE when they are set);
+ * opts->per_vertex_out must be NULL. Because it only enqueues kernels and
+ * copies on one stream, the call can be captured into a CUDA graph and
+ * replayed. The handle's plan scratch is shared by its calls: calls on one
+ * handle must not overlap on the GPU. opts->timeout_ms is ignored.
+ * Errors: EINVAL when no plan matches or an output is not allowed; ECUDA.
+ */
+bbtc_status bbtc_count_async(bbtc_graph_t g, const bbtc_opts *opts, uint64_t *total_dev);
+
 /* Free the handle and its device memory. Accepts NULL. */
 void bbtc_graph_destroy(bbtc_graph_t g);
 
@@ -185,6 +231,7 @@ typedef struct {
   uint64_t device_bytes; /* device memory held by the handle */
   uint64_t wedges_in;    /* sum over oriented edges (u,v) of d+(v) */
   uint64_t wedges_out;   /* sum over vertices u of d+(u)(d+(u)-1)/2 */
+  int64_t num_graphs;    /* graphs in the handle (1 unless built as a batch) */
 } bbtc_graph_info;
 
 /* Sizes and work figures of the handle's graph (the two wedge sums are

@@ -23,6 +23,7 @@ __all__ = [
     "bbtc_count_batch", "bbtc_graph_destroy", "bbtc_last_error", "bbtc_num_tasks",
     "bbtc_opts_init", "bbtc_graph_get_info", "bbtc_graph_get_oriented", "bbtc_graph_get_plan",
     "bbtc_graph_get_timings", "bbtc_kernel_launches", "bbtc_count_noalloc",
+    "bbtc_graph_create_batch", "bbtc_count_async", "BatchGraph",
     "library_path", "load",
 ]
 
@@ -53,6 +54,9 @@ class bbtc_opts(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("flags", ctypes.c_uint32),
         ("hash_threshold", ctypes.c_int32),
+        ("per_graph_out", ctypes.c_void_p),
+        ("chunk", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -65,6 +69,7 @@ class bbtc_graph_info(ctypes.Structure):
         ("device_bytes", ctypes.c_uint64),
         ("wedges_in", ctypes.c_uint64),
         ("wedges_out", ctypes.c_uint64),
+        ("num_graphs", ctypes.c_int64),
     ]
 
 
@@ -124,6 +129,10 @@ def load():
         lib.bbtc_kernel_launches.restype = u64
         lib.bbtc_count_noalloc.argtypes = [P, i32, P, P, P]
         lib.bbtc_count_noalloc.restype = st
+        lib.bbtc_graph_create_batch.argtypes = [i32, P, P, P, u32, P, ctypes.POINTER(P)]
+        lib.bbtc_graph_create_batch.restype = st
+        lib.bbtc_count_async.argtypes = [P, ctypes.POINTER(bbtc_opts), P]
+        lib.bbtc_count_async.restype = st
         _lib = lib
         return lib
 
@@ -198,20 +207,23 @@ def bbtc_graph_destroy(handle: int) -> None:
 
 def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
               device_budget_bytes: int = 0, per_vertex_out=None, per_task_out=None,
-              stream=None, hash_threshold: int = 0) -> bbtc_opts:
+              stream=None, hash_threshold: int = 0, per_graph_out=None,
+              chunk: int = 0) -> bbtc_opts:
     o = bbtc_opts_init()
     o.p = p
     o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     o.timeout_ms = timeout_ms
     o.device_budget_bytes = device_budget_bytes
     o.hash_threshold = hash_threshold
-    pv, pv_dev = _ptr(per_vertex_out)
-    pt, pt_dev = _ptr(per_task_out)
-    if (per_vertex_out is not None and per_task_out is not None) and pv_dev != pt_dev:
-        raise ValueError("per-vertex and per-task outputs must both be host or both device")
-    o.per_vertex_out = pv or None
-    o.per_task_out = pt or None
-    o.flags = OUT_DEVICE if (pv_dev or pt_dev) else 0
+    o.chunk = chunk
+    outs = [(_ptr(a), a is not None) for a in (per_vertex_out, per_task_out, per_graph_out)]
+    kinds = {dev for (addr, dev), given in outs if given}
+    if len(kinds) > 1:
+        raise ValueError("optional outputs must all be host arrays or all device arrays")
+    o.per_vertex_out = outs[0][0][0] or None
+    o.per_task_out = outs[1][0][0] or None
+    o.per_graph_out = outs[2][0][0] or None
+    o.flags = OUT_DEVICE if kinds == {True} else 0
     o.stream = _stream_ptr(stream) or None
     return o
 
@@ -221,6 +233,28 @@ def bbtc_count(handle: int, opts: bbtc_opts | None = None) -> int:
     _check(load().bbtc_count(handle, ctypes.byref(opts) if opts is not None else None,
                              ctypes.byref(c)))
     return int(c.value)
+
+
+def bbtc_graph_create_batch(vertex_offsets, rowptr, colidx, flags: int = 0, stream=None) -> int:
+    """One handle for a batch: vertex_offsets (host int64, ng+1), union rowptr, LOCAL colidx."""
+    voff = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+    ng = voff.shape[0] - 1
+    rp, rp_dev = _ptr(rowptr)
+    ci, ci_dev = _ptr(colidx)
+    if rp_dev or ci_dev:
+        flags |= INPUT_DEVICE
+    h = ctypes.c_void_p()
+    _check(load().bbtc_graph_create_batch(ng, voff.ctypes.data, rp or None, ci or None, flags,
+                                          _stream_ptr(stream) or None, ctypes.byref(h)))
+    return h.value
+
+
+def bbtc_count_async(handle: int, opts: bbtc_opts, total_dev) -> None:
+    """Enqueue a count into device buffers (no allocation, no wait; capturable)."""
+    t, t_dev = _ptr(total_dev)
+    if not t_dev:
+        raise ValueError("bbtc_count_async writes device buffers only")
+    _check(load().bbtc_count_async(handle, ctypes.byref(opts), t))
 
 
 def bbtc_count_noalloc(handle: int, p: int, count_dev, per_task_dev=None, stream=None) -> None:
@@ -298,22 +332,26 @@ class Graph:
 
     def count(self, p: int = 0, kernel: str = "auto", per_vertex: bool = False,
               per_task: bool = False, timeout_ms: int = 0, device_budget_bytes: int = 0,
-              stream=None, hash_threshold: int = 0):
-        """Total triangle count, or a dict with per-task / per-vertex counts."""
+              stream=None, hash_threshold: int = 0, per_graph: bool = False, chunk: int = 0):
+        """Total triangle count, or a dict with per-task / per-vertex / per-graph counts."""
         pt = np.zeros(max(bbtc_num_tasks(p), 1), dtype=np.uint64) if per_task and p > 0 else None
         if per_task and p == 0:
             raise ValueError("per_task needs an explicit p")
         pv = np.zeros(max(self.n, 1), dtype=np.uint64) if per_vertex else None
+        ng = self.info()["num_graphs"] if per_graph else 0
+        pg = np.zeros(max(ng, 1), dtype=np.uint64) if per_graph else None
         opts = make_opts(p, kernel, timeout_ms, device_budget_bytes, pv, pt, stream,
-                         hash_threshold)
+                         hash_threshold, pg, chunk)
         total = bbtc_count(self.handle, opts)
-        if not per_task and not per_vertex:
+        if not per_task and not per_vertex and not per_graph:
             return total
         out = {"total": total}
         if per_task:
             out["per_task"] = pt[:bbtc_num_tasks(p)]
         if per_vertex:
             out["per_vertex"] = pv[:self.n]
+        if per_graph:
+            out["per_graph"] = pg[:ng]
         return out
 
     def info(self) -> dict:
@@ -344,3 +382,34 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def batch_csr(graphs):
+    """Concatenate [(n, rowptr, colidx), ...] into (vertex_offsets, rowptr, colidx) with
+    colidx left local to each graph (the form bbtc_graph_create_batch takes)."""
+    ns = [int(g[0]) for g in graphs]
+    voff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    voff[1:] = np.cumsum(ns)
+    nnz = [int(g[1][g[0]]) for g in graphs]
+    eoff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    eoff[1:] = np.cumsum(nnz)
+    rowptr = np.empty(int(voff[-1]) + 1, dtype=np.int64)
+    colidx = np.empty(int(eoff[-1]), dtype=np.int32)
+    for i, (n, rp, ci) in enumerate(graphs):
+        rowptr[voff[i]:voff[i] + n] = np.asarray(rp[:n], dtype=np.int64) + eoff[i]
+        colidx[eoff[i]:eoff[i + 1]] = ci[:nnz[i]]
+    rowptr[-1] = eoff[-1]
+    return voff, rowptr, colidx
+
+
+class BatchGraph(Graph):
+    """A batch handle: several independent graphs prepared and counted as one union."""
+
+    def __init__(self, graphs=None, vertex_offsets=None, rowptr=None, colidx=None,
+                 symmetric: bool = False, stream=None):
+        if graphs is not None:
+            vertex_offsets, rowptr, colidx = batch_csr(graphs)
+        flags = INPUT_SYMMETRIC if symmetric else 0
+        self.handle = bbtc_graph_create_batch(vertex_offsets, rowptr, colidx, flags, stream)
+        self.n = int(np.asarray(vertex_offsets)[-1])
+        self.num_graphs = len(vertex_offsets) - 1

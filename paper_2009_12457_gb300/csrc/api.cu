@@ -93,6 +93,8 @@ void destroy_graph(bbtc_graph *g) {
   dfree(g->esrc, s);
   dfree(g->perm, s);
   dfree(g->deg, s);
+  dfree(g->voff, s);
+  dfree(g->gid, s);
   cudaStreamSynchronize(s);
   for (cudaEvent_t &e : g->ev)
     if (e) cudaEventDestroy(e);
@@ -131,8 +133,17 @@ bbtc_status check_opts(const bbtc_opts *opts, bbtc_opts *out) {
     return BBTC_EINVAL;
   }
   if (out->hash_threshold == 0) out->hash_threshold = 16;
+  if (out->chunk < 0 || out->reserved != 0) {
+    set_error("chunk = %d must be >= 0 and reserved must be 0", out->chunk);
+    return BBTC_EINVAL;
+  }
   return BBTC_OK;
 }
+
+// Shared body of bbtc_graph_create_async and bbtc_graph_create_batch.
+bbtc_status create_common(int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                          uint32_t flags, void *stream, int32_t ng, const int64_t *voff_host,
+                          bbtc_graph_t *out);
 
 }  // namespace
 }  // namespace bbtc
@@ -155,9 +166,14 @@ uint64_t bbtc_num_tasks(int32_t p) {
   return (uint64_t)p * (uint64_t)(p + 1) * (uint64_t)(p + 2) / 6;
 }
 
-bbtc_status bbtc_graph_create_async(int64_t n, const int64_t *rowptr, const int32_t *colidx,
-                                    uint32_t flags, void *stream, bbtc_graph_t *out) {
-  clear_error();
+}  // extern "C"
+
+namespace bbtc {
+namespace {
+
+bbtc_status create_common(int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                          uint32_t flags, void *stream, int32_t ng, const int64_t *voff_host,
+                          bbtc_graph_t *out) {
   if (!out) {
     set_error("bbtc_graph_create: out is NULL");
     return BBTC_EINVAL;
@@ -182,6 +198,7 @@ bbtc_status bbtc_graph_create_async(int64_t n, const int64_t *rowptr, const int3
   }
   cudaGetDevice(&g->device);
   g->n = n;
+  g->ng = ng;
   if (stream) {
     g->stream = (cudaStream_t)stream;
   } else {
@@ -201,6 +218,16 @@ bbtc_status bbtc_graph_create_async(int64_t n, const int64_t *rowptr, const int3
     }
   }
   bbtc_status st = BBTC_OK;
+  if (voff_host) {
+    if (dalloc_n(&g->voff, ng + 1, s) != BBTC_OK ||
+        cudaMemcpyAsync(g->voff, voff_host, sizeof(int64_t) * (size_t)(ng + 1),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_error("bbtc_graph_create_batch: copying the vertex offsets failed");
+      destroy_graph(g);
+      return BBTC_ENOMEM;
+    }
+    g->bytes += (uint64_t)(ng + 1) * 8;
+  }
   int64_t nnz = 0;
   int64_t *d_rowptr = nullptr;
   int32_t *d_colidx = nullptr;
@@ -270,6 +297,38 @@ bbtc_status bbtc_graph_create_async(int64_t n, const int64_t *rowptr, const int3
   return BBTC_OK;
 }
 
+}  // namespace
+}  // namespace bbtc
+
+extern "C" {
+
+bbtc_status bbtc_graph_create_async(int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                                    uint32_t flags, void *stream, bbtc_graph_t *out) {
+  clear_error();
+  return create_common(n, rowptr, colidx, flags, stream, 1, nullptr, out);
+}
+
+bbtc_status bbtc_graph_create_batch(int32_t ng, const int64_t *vertex_offsets,
+                                    const int64_t *rowptr, const int32_t *colidx, uint32_t flags,
+                                    void *stream, bbtc_graph_t *out) {
+  clear_error();
+  if (ng < 1 || !vertex_offsets) {
+    set_error("bbtc_graph_create_batch: ng = %d must be >= 1 with vertex offsets", ng);
+    return BBTC_EINVAL;
+  }
+  if (vertex_offsets[0] != 0) {
+    set_error("bbtc_graph_create_batch: vertex_offsets[0] must be 0");
+    return BBTC_EINVAL;
+  }
+  for (int32_t i = 0; i < ng; ++i)
+    if (vertex_offsets[i + 1] < vertex_offsets[i]) {
+      set_error("bbtc_graph_create_batch: vertex_offsets decrease at graph %d", i);
+      return BBTC_EINVAL;
+    }
+  return create_common(vertex_offsets[ng], rowptr, colidx, flags, stream, ng, vertex_offsets,
+                       out);
+}
+
 bbtc_status bbtc_graph_create(int64_t n, const int64_t *rowptr, const int32_t *colidx,
                               uint32_t flags, bbtc_graph_t *out) {
   return bbtc_graph_create_async(n, rowptr, colidx, flags, nullptr, out);
@@ -301,45 +360,79 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
       return BBTC_ENOMEM;
     }
   }
-  const bool rebuild = !(g->plan.p == p && g->plan.kernel_mode == opts.kernel &&
-                         g->plan.hash_threshold == opts.hash_threshold);
+  const bool rebuild = !plan_matches(g->plan, p, opts.kernel, opts.hash_threshold, opts.chunk);
   if (rebuild) BBTC_CUDA(cudaEventRecord(g->ev[2], s));
-  BBTC_TRY(build_plan(g, p, opts.kernel, opts.hash_threshold, s));
+  BBTC_TRY(build_plan(g, p, opts.kernel, opts.hash_threshold, opts.chunk, s));
   if (rebuild) BBTC_CUDA(cudaEventRecord(g->ev[3], s));
   g->plan_timed = rebuild;
   const Plan &pl = g->plan;
   Scratch scratch(s);
-  CountOutputs out;
-  BBTC_TRY(scratch.get(&out.task_count, pl.ntasks));
-  BBTC_TRY(scratch.get(&out.total, 1));
-  BBTC_TRY(scratch.get(&out.status, 1));
-  if (opts.per_vertex_out) BBTC_TRY(scratch.get(&out.vertex_count, g->n));
-  BBTC_TRY(run_count(g, pl, out, opts.timeout_ms, s, g->ev[4], g->ev[5]));
-  unsigned long long total = 0;
-  int32_t status = 0;
-  BBTC_CUDA(cudaMemcpyAsync(&total, out.total, sizeof(total), cudaMemcpyDeviceToHost, s));
-  BBTC_CUDA(cudaMemcpyAsync(&status, out.status, sizeof(status), cudaMemcpyDeviceToHost, s));
+  unsigned long long *vertex_count = nullptr;
+  if (opts.per_vertex_out) BBTC_TRY(scratch.get(&vertex_count, g->n));
+  const bool per_graph = opts.per_graph_out != nullptr;
+  BBTC_TRY(run_count(g, pl, vertex_count, per_graph, opts.timeout_ms, s, g->ev[4], g->ev[5]));
+  unsigned long long head[SCR_TASKS] = {0, 0, 0};
+  BBTC_CUDA(cudaMemcpyAsync(head, pl.scratch, sizeof(head), cudaMemcpyDeviceToHost, s));
   BBTC_CUDA(cudaStreamSynchronize(s));
-  if (status != 0) {
+  if ((int32_t)head[SCR_STATUS] != 0) {
     set_error("bbtc_count: the counting kernel passed its %u ms limit", opts.timeout_ms);
     return BBTC_ETIMEOUT;
   }
   const bool out_dev = (opts.flags & BBTC_OUT_DEVICE) != 0;
   const cudaMemcpyKind kind = out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (opts.per_task_out)
-    BBTC_CUDA(cudaMemcpyAsync(opts.per_task_out, out.task_count,
+    BBTC_CUDA(cudaMemcpyAsync(opts.per_task_out, pl.scratch + SCR_TASKS,
                               sizeof(uint64_t) * (size_t)pl.ntasks, kind, s));
+  if (per_graph)
+    BBTC_CUDA(cudaMemcpyAsync(opts.per_graph_out, pl.scratch + SCR_TASKS + pl.ntasks,
+                              sizeof(uint64_t) * (size_t)g->ng, kind, s));
   if (opts.per_vertex_out && g->n > 0) {
     unsigned long long *by_id = nullptr;
     BBTC_TRY(scratch.get(&by_id, g->n));
-    k_scatter_by_perm<<<grid_for(g->n, 256, 16), 256, 0, s>>>(out.vertex_count, g->perm, g->n,
+    k_scatter_by_perm<<<grid_for(g->n, 256, 16), 256, 0, s>>>(vertex_count, g->perm, g->n,
                                                               by_id);
     BBTC_LAUNCH_CHECK();
     BBTC_CUDA(cudaMemcpyAsync(opts.per_vertex_out, by_id, sizeof(uint64_t) * (size_t)g->n, kind,
                               s));
   }
   BBTC_CUDA(cudaStreamSynchronize(s));
-  *count = total;
+  *count = head[SCR_TOTAL];
+  return BBTC_OK;
+}
+
+bbtc_status bbtc_count_async(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *total_dev) {
+  clear_error();
+  if (!g || !total_dev) {
+    set_error("bbtc_count_async: NULL handle or total_dev");
+    return BBTC_EINVAL;
+  }
+  bbtc_opts opts;
+  BBTC_TRY(check_opts(opts_in, &opts));
+  const int p = opts.p == 0 ? default_p(g) : opts.p;
+  if (!plan_matches(g->plan, p, opts.kernel, opts.hash_threshold, opts.chunk)) {
+    set_error("bbtc_count_async: no plan for these options on the handle; build it with "
+              "bbtc_count or bbtc_graph_get_plan first");
+    return BBTC_EINVAL;
+  }
+  if (opts.per_vertex_out ||
+      ((opts.per_task_out || opts.per_graph_out) && !(opts.flags & BBTC_OUT_DEVICE))) {
+    set_error("bbtc_count_async: outputs must be device pointers (BBTC_OUT_DEVICE) and "
+              "per_vertex_out must be NULL");
+    return BBTC_EINVAL;
+  }
+  DeviceGuard dg(g->device);
+  cudaStream_t s = opts.stream ? (cudaStream_t)opts.stream : g->stream;
+  const Plan &pl = g->plan;
+  const bool per_graph = opts.per_graph_out != nullptr;
+  BBTC_TRY(run_count(g, pl, nullptr, per_graph, 0, s, nullptr, nullptr));
+  BBTC_CUDA(cudaMemcpyAsync(total_dev, pl.scratch + SCR_TOTAL, sizeof(uint64_t),
+                            cudaMemcpyDeviceToDevice, s));
+  if (opts.per_task_out)
+    BBTC_CUDA(cudaMemcpyAsync(opts.per_task_out, pl.scratch + SCR_TASKS,
+                              sizeof(uint64_t) * (size_t)pl.ntasks, cudaMemcpyDeviceToDevice, s));
+  if (per_graph)
+    BBTC_CUDA(cudaMemcpyAsync(opts.per_graph_out, pl.scratch + SCR_TASKS + pl.ntasks,
+                              sizeof(uint64_t) * (size_t)g->ng, cudaMemcpyDeviceToDevice, s));
   return BBTC_OK;
 }
 
@@ -350,19 +443,61 @@ bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts
     set_error("bbtc_count_batch: invalid arguments");
     return BBTC_EINVAL;
   }
+  if (ng == 0) return BBTC_OK;
   bbtc_opts o;
   BBTC_TRY(check_opts(opts, &o));
-  o.per_task_out = nullptr;
-  o.per_vertex_out = nullptr;
+  // NULL handles are reported and skipped; the rest are counted together
+  bbtc_graph_t *valid = new (std::nothrow) bbtc_graph_t[(size_t)ng];
+  int32_t *where = new (std::nothrow) int32_t[(size_t)ng];
+  if (!valid || !where) {
+    delete[] valid;
+    delete[] where;
+    set_error("bbtc_count_batch: host allocation failed");
+    return BBTC_ENOMEM;
+  }
+  int32_t nv = 0;
   bbtc_status first = BBTC_OK;
   for (int32_t i = 0; i < ng; ++i) {
-    uint64_t c = 0;
-    bbtc_status st = gs[i] ? bbtc_count(gs[i], &o, &c) : BBTC_EINVAL;
-    if (per_graph) per_graph[i] = st;
-    if (st == BBTC_OK) counts[i] = c;
-    else if (first == BBTC_OK) first = st;
+    if (gs[i]) {
+      where[nv] = i;
+      valid[nv++] = gs[i];
+      if (per_graph) per_graph[i] = BBTC_OK;
+    } else {
+      if (per_graph) per_graph[i] = BBTC_EINVAL;
+      if (first == BBTC_OK) {
+        first = BBTC_EINVAL;
+        set_error("bbtc_count_batch: handle %d is NULL", i);
+      }
+    }
   }
-  return first;
+  bbtc_status st = BBTC_OK;
+  if (nv > 0) {
+    DeviceGuard dg(valid[0]->device);
+    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : valid[0]->stream;
+    bbtc_graph *u = nullptr;
+    st = union_of(valid, nv, s, &u);
+    uint64_t *sub = st == BBTC_OK ? new (std::nothrow) uint64_t[(size_t)nv] : nullptr;
+    if (st == BBTC_OK && !sub) st = BBTC_ENOMEM;
+    if (st == BBTC_OK) {
+      bbtc_opts uo = o;
+      uo.per_task_out = nullptr;
+      uo.per_vertex_out = nullptr;
+      uo.per_graph_out = sub;
+      uo.flags = 0;
+      uo.stream = s;
+      uint64_t total = 0;
+      st = bbtc_count(u, &uo, &total);
+      if (st == BBTC_OK)
+        for (int32_t x = 0; x < nv; ++x) counts[where[x]] = sub[x];
+    }
+    if (st != BBTC_OK && per_graph)
+      for (int32_t x = 0; x < nv; ++x) per_graph[where[x]] = st;
+    delete[] sub;
+    if (u) destroy_graph(u);
+  }
+  delete[] valid;
+  delete[] where;
+  return st != BBTC_OK ? st : first;
 }
 
 bbtc_status bbtc_graph_get_info(bbtc_graph_t g, bbtc_graph_info *info) {
@@ -383,6 +518,7 @@ bbtc_status bbtc_graph_get_info(bbtc_graph_t g, bbtc_graph_info *info) {
   }
   info->wedges_in = g->wedges_in;
   info->wedges_out = g->wedges_out;
+  info->num_graphs = g->ng;
   return BBTC_OK;
 }
 
@@ -465,7 +601,8 @@ bbtc_status bbtc_graph_get_plan(bbtc_graph_t g, int32_t p, int32_t *cuts, int64_
   cudaStream_t s = g->stream;
   const int kmode = g->plan.p == p ? g->plan.kernel_mode : BBTC_KERNEL_AUTO;
   const int thr = g->plan.p == p ? g->plan.hash_threshold : 16;
-  BBTC_TRY(build_plan(g, p, kmode, thr, s));
+  const int chunk = g->plan.p == p ? g->plan.chunk_req : 0;
+  BBTC_TRY(build_plan(g, p, kmode, thr, chunk, s));
   const Plan &pl = g->plan;
   if (cuts)
     BBTC_CUDA(cudaMemcpyAsync(cuts, pl.cuts, sizeof(int32_t) * (size_t)(p + 1),

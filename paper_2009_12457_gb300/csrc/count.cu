@@ -34,10 +34,14 @@ struct CountParams {
   int64_t nitems;
   unsigned long long *head;
   unsigned long long *task_count;
-  unsigned long long *vcount;
+  unsigned long long *vcount;       // per-vertex counts by position (MODE & 1)
+  const int32_t *gid;               // graph of each position (MODE & 2)
+  unsigned long long *graph_count;  // per-graph counts (MODE & 2)
   int32_t *status;
   uint64_t timeout_ns;
 };
+
+constexpr int MODE_VERTEX = 1, MODE_GRAPH = 2;
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -91,8 +95,10 @@ struct LaneRec {
 
 constexpr int UNIFORM_MIN = 4;  // a run of >= 4 in-edges into one v is a uniform batch
 
-template <bool PER_VERTEX>
+template <int MODE>
 __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
+  constexpr bool PER_VERTEX = (MODE & MODE_VERTEX) != 0;
+  constexpr bool PER_GRAPH = (MODE & MODE_GRAPH) != 0;
   extern __shared__ __align__(16) unsigned char count_smem_raw[];
   __shared__ int32_t cuts[MAXP + 1];
   for (int i = threadIdx.x; i <= P.p; i += CT_NT) cuts[i] = P.cuts[i];
@@ -226,64 +232,66 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
         }
       }
 
-      // each lane walks a contiguous run of the flattened probes
+      // flattened probes, interleaved over the lanes (lanes that share an
+      // in-edge read consecutive elements); each lane's owner only moves
+      // forward, at most 31 steps per batch
       rec.s0[lane] = s0;
       rec.incl[lane] = incl;
       if (!uniform) {
         rec.b0[lane] = b0;
         rec.b1[lane] = b1;
       }
-      if (PER_VERTEX) {
+      if (PER_VERTEX || PER_GRAPH) {
         rec.u[lane] = u;
         rec.v[lane] = uniform ? v0 : v;
       }
       __syncwarp();
-      const uint32_t per = (total + 31) >> 5;
-      const uint32_t qa = lane * per;
-      const uint32_t qb = qa + per < total ? qa + per : total;
-      if (qa < qb) {
-        // owner of qa: the first lane whose inclusive prefix exceeds qa
-        int o = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (rec.incl[o + step - 1] <= qa) o += step;
-        uint32_t o_end = rec.incl[o];
-        // addr + q indexes colidx for every q owned by o
-        int64_t addr = rec.s0[o] - (int64_t)(o == 0 ? 0 : rec.incl[o - 1]);
-        int64_t lo = b0, hi = b1;
-        if (!uniform) {
-          lo = rec.b0[o];
-          hi = rec.b1[o];
-        }
-        for (uint32_t q = qa; q < qb; ++q) {
-          while (q >= o_end) {
-            ++o;
-            const uint32_t prev_end = o_end;
-            o_end = rec.incl[o];
-            addr = rec.s0[o] - (int64_t)prev_end;
-            if (!uniform) {
-              lo = rec.b0[o];
-              hi = rec.b1[o];
-            }
-          }
-          const int32_t wv = col[addr + q];
-          bool hit;
-          if (staged) {
-            hit = staged_hash ? hash_contains(stage, staged_log2h, wv)
-                              : sorted_contains(stage, staged_len, wv);
-          } else {
-            const int64_t pos = lower_bound_dev<int32_t, int64_t>(col, lo, hi, wv);
-            hit = pos < hi && col[pos] == wv;
-          }
-          if (hit) {
-            ++acc;
-            if (PER_VERTEX) {
-              atomicAdd(&P.vcount[rec.u[o]], 1ull);
-              atomicAdd(&P.vcount[rec.v[o]], 1ull);
-              atomicAdd(&P.vcount[wv], 1ull);
-            }
+      unsigned long long batch_hits = 0;  // one graph per uniform batch
+      int o = 0;
+      uint32_t o_end = rec.incl[0];
+      int64_t addr = rec.s0[0];  // colidx index of probe q is addr + q
+      int64_t lo = b0, hi = b1;
+      if (!uniform) {
+        lo = rec.b0[0];
+        hi = rec.b1[0];
+      }
+      for (uint32_t q = lane; q < total; q += 32) {
+        while (q >= o_end) {
+          ++o;
+          const uint32_t prev_end = o_end;
+          o_end = rec.incl[o];
+          addr = rec.s0[o] - (int64_t)prev_end;
+          if (!uniform) {
+            lo = rec.b0[o];
+            hi = rec.b1[o];
           }
         }
+        const int32_t wv = col[addr + q];
+        bool hit;
+        if (staged) {
+          hit = staged_hash ? hash_contains(stage, staged_log2h, wv)
+                            : sorted_contains(stage, staged_len, wv);
+        } else {
+          const int64_t pos = lower_bound_dev<int32_t, int64_t>(col, lo, hi, wv);
+          hit = pos < hi && col[pos] == wv;
+        }
+        if (hit) {
+          ++acc;
+          if (PER_VERTEX) {
+            atomicAdd(&P.vcount[rec.u[o]], 1ull);
+            atomicAdd(&P.vcount[rec.v[o]], 1ull);
+            atomicAdd(&P.vcount[wv], 1ull);
+          }
+          if (PER_GRAPH) {
+            // every in-edge into v comes from v's own graph
+            if (uniform) ++batch_hits;
+            else atomicAdd(&P.graph_count[P.gid[rec.v[o]]], 1ull);
+          }
+        }
+      }
+      if (PER_GRAPH && uniform) {
+        batch_hits = warp_sum(batch_hits);
+        if (lane == 0 && batch_hits) atomicAdd(&P.graph_count[P.gid[v0]], batch_hits);
       }
       __syncwarp();
     }
@@ -323,13 +331,30 @@ __global__ void k_wedges(const int64_t *__restrict__ rowptr, const int32_t *__re
   }
 }
 
-int g_count_blocks[2] = {0, 0};
-
 size_t count_smem_bytes() {
   return (size_t)(CT_NT / 32) * (STAGE * sizeof(int32_t) + sizeof(LaneRec));
 }
 
+template <int MODE>
+bbtc_status configure_mode(int *blocks_per_sm) {
+  const size_t smem = count_smem_bytes();
+  BBTC_CUDA(cudaFuncSetAttribute(k_count<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  BBTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_count<MODE>, CT_NT,
+                                                          smem));
+  if (*blocks_per_sm < 1) *blocks_per_sm = 1;
+  return BBTC_OK;
+}
+
 }  // namespace
+
+bbtc_status configure_count_kernels(Plan *pl) {
+  BBTC_TRY(configure_mode<0>(&pl->blocks_per_sm[0]));
+  BBTC_TRY(configure_mode<1>(&pl->blocks_per_sm[1]));
+  BBTC_TRY(configure_mode<2>(&pl->blocks_per_sm[2]));
+  BBTC_TRY(configure_mode<3>(&pl->blocks_per_sm[3]));
+  return BBTC_OK;
+}
 
 bbtc_status wedge_sums(const bbtc_graph *g, uint64_t *in_sum, uint64_t *out_sum,
                        cudaStream_t s) {
@@ -351,21 +376,19 @@ bbtc_status wedge_sums(const bbtc_graph *g, uint64_t *in_sum, uint64_t *out_sum,
   return BBTC_OK;
 }
 
-bbtc_status run_count(bbtc_graph *g, const Plan &pl, const CountOutputs &out,
-                      uint32_t timeout_ms, cudaStream_t s, cudaEvent_t ev_begin,
-                      cudaEvent_t ev_end) {
+bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
+                      bool per_graph, uint32_t timeout_ms, cudaStream_t s,
+                      cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   const int64_t nt = pl.ntasks;
-  BBTC_CUDA(cudaMemsetAsync(out.task_count, 0, sizeof(unsigned long long) * (size_t)nt, s));
-  BBTC_CUDA(cudaMemsetAsync(out.total, 0, sizeof(unsigned long long), s));
-  BBTC_CUDA(cudaMemsetAsync(out.status, 0, sizeof(int32_t), s));
-  if (out.vertex_count)
-    BBTC_CUDA(cudaMemsetAsync(out.vertex_count, 0,
+  const int ng = per_graph ? g->ng : 0;
+  unsigned long long *scr = pl.scratch;
+  BBTC_CUDA(cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (size_t)(SCR_TASKS + nt + ng),
+                            s));
+  if (vertex_count)
+    BBTC_CUDA(cudaMemsetAsync(vertex_count, 0,
                               sizeof(unsigned long long) * (size_t)(g->n > 0 ? g->n : 1), s));
+  if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
   if (pl.nitems > 0) {
-    Scratch scratch(s);
-    unsigned long long *head = nullptr;
-    BBTC_TRY(scratch.get(&head, 1));
-    BBTC_CUDA(cudaMemsetAsync(head, 0, sizeof(unsigned long long), s));
     CountParams P;
     P.rowptr = g->rowptr;
     P.colidx = g->colidx;
@@ -377,43 +400,28 @@ bbtc_status run_count(bbtc_graph *g, const Plan &pl, const CountOutputs &out,
     P.tasks = pl.tasks;
     P.items = pl.items;
     P.nitems = pl.nitems;
-    P.head = head;
-    P.task_count = out.task_count;
-    P.vcount = out.vertex_count;
-    P.status = out.status;
+    P.head = scr + SCR_HEAD;
+    P.task_count = scr + SCR_TASKS;
+    P.vcount = vertex_count;
+    P.gid = g->gid;
+    P.graph_count = scr + SCR_TASKS + nt;
+    P.status = reinterpret_cast<int32_t *>(scr + SCR_STATUS);
     P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
-    const bool pv = out.vertex_count != nullptr;
-    const size_t smem = count_smem_bytes();
-    int &blocks_per_sm = g_count_blocks[pv];
-    if (!blocks_per_sm) {
-      if (pv) {
-        BBTC_CUDA(cudaFuncSetAttribute(k_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-        BBTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_count<true>,
-                                                                CT_NT, smem));
-      } else {
-        BBTC_CUDA(cudaFuncSetAttribute(k_count<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        BBTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_count<false>,
-                                                                CT_NT, smem));
-      }
-      if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
-    int64_t blocks = (int64_t)num_sms() * blocks_per_sm;
+    const int mode = (vertex_count ? MODE_VERTEX : 0) | (per_graph ? MODE_GRAPH : 0);
+    int64_t blocks = (int64_t)num_sms() * pl.blocks_per_sm[mode];
     const int64_t need = (pl.nitems + CT_NT / 32 - 1) / (CT_NT / 32);
     if (blocks > need) blocks = need;
-    if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
-    if (pv)
-      k_count<true><<<(unsigned)blocks, CT_NT, smem, s>>>(P);
-    else
-      k_count<false><<<(unsigned)blocks, CT_NT, smem, s>>>(P);
+    const size_t smem = count_smem_bytes();
+    switch (mode) {
+      case 0: k_count<0><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+      case 1: k_count<1><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+      case 2: k_count<2><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+      default: k_count<3><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+    }
     BBTC_LAUNCH_CHECK();
-    if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
-  } else {
-    if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
-    if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
   }
-  k_sum_u64<<<grid_for(nt, 256, 2), 256, 0, s>>>(out.task_count, nt, out.total);
+  if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
+  k_sum_u64<<<grid_for(nt, 256, 2), 256, 0, s>>>(scr + SCR_TASKS, nt, scr + SCR_TOTAL);
   BBTC_LAUNCH_CHECK();
   return BBTC_OK;
 }
@@ -514,13 +522,15 @@ extern "C" bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *c
       P.head = scratch + NOALLOC_HEAD;
       P.task_count = task_count;
       P.vcount = nullptr;
+      P.gid = nullptr;
+      P.graph_count = nullptr;
       P.status = reinterpret_cast<int32_t *>(scratch + NOALLOC_STATUS);
       P.timeout_ns = 0;
       const size_t smem = count_smem_bytes();
       int blocks_per_sm = 0;
-      if (cudaFuncSetAttribute(k_count<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if (cudaFuncSetAttribute(k_count<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_count<false>, CT_NT,
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_count<0>, CT_NT,
                                                         smem) != cudaSuccess) {
         set_error("bbtc_count_noalloc: kernel configuration failed");
         st = BBTC_ECUDA;
@@ -530,7 +540,7 @@ extern "C" bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *c
       int64_t blocks = (int64_t)num_sms() * blocks_per_sm;
       const int64_t need = (pl.nitems + CT_NT / 32 - 1) / (CT_NT / 32);
       if (blocks > need) blocks = need;
-      k_count<false><<<(unsigned)blocks, CT_NT, smem, s>>>(P);
+      k_count<0><<<(unsigned)blocks, CT_NT, smem, s>>>(P);
       if ((st = launch_status("bbtc_count_noalloc")) != BBTC_OK) break;
     }
     k_sum_u64<<<grid_for(nt, 256, 2), 256, 0, s>>>(

@@ -30,8 +30,16 @@ struct Plan {
   WorkItem *items = nullptr;    // work items, heaviest task first
   int32_t kernel_mode = -1;     // bbtc_kernel the items were built for
   int32_t hash_threshold = 0;
+  int32_t chunk_req = 0;        // requested in-edges per item (0 = automatic)
+  int64_t chunk = 0;            // in-edges per item used
+  // counting scratch owned by the plan: [0] work-stealing head, [1] status,
+  // [2] total, [3, 3+T) per-task counts, [3+T, 3+T+ng) per-graph counts
+  unsigned long long *scratch = nullptr;
+  int blocks_per_sm[4] = {0, 0, 0, 0};  // occupancy of each counting-kernel mode
   uint64_t bytes = 0;
 };
+
+constexpr int SCR_HEAD = 0, SCR_STATUS = 1, SCR_TOTAL = 2, SCR_TASKS = 3;
 
 }  // namespace bbtc
 
@@ -49,6 +57,9 @@ struct bbtc_graph {
   int32_t *deg = nullptr;      // n, undirected simple degree by original id
   int64_t dplus_max = 0;
   int64_t deg_max = 0;
+  int32_t ng = 1;              // graphs in the handle (a batch is their disjoint union)
+  int64_t *voff = nullptr;     // device, ng+1 vertex offsets (batch handles only)
+  int32_t *gid = nullptr;      // device, n: graph of each position (batch handles only)
   uint64_t bytes = 0;
   bbtc::Plan plan;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -60,30 +71,40 @@ struct bbtc_graph {
 namespace bbtc {
 
 // a1-a4: build g's oriented CSR from an input CSR already on the device.
+// For a batch handle (g->ng > 1, g->voff set), colidx holds ids local to each
+// row's graph; they are offset into the union and g->gid is filled.
 bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t *d_colidx,
                           int64_t nnz, bool symmetric);
 
 // a5-a8: partition, blocks, tasks, estimate, order and work items for p.
-bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold,
+bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold, int chunk,
                        cudaStream_t s);
+inline bool plan_matches(const Plan &pl, int p, int kernel_mode, int hash_threshold, int chunk) {
+  return pl.p == p && pl.kernel_mode == kernel_mode && pl.hash_threshold == hash_threshold &&
+         pl.chunk_req == chunk;
+}
 void free_plan(Plan *pl, cudaStream_t s);
 
-// a9-a10: per-task counts (device, Alg. 4 order) and optional per-vertex
-// counts by position; *total_dev receives the sum.
-struct CountOutputs {
-  unsigned long long *task_count = nullptr;  // device, T
-  unsigned long long *vertex_count = nullptr;  // device, n (by position) or null
-  unsigned long long *total = nullptr;  // device, 1
-  int32_t *status = nullptr;            // device, 1: 0 ok, 1 timeout
-};
-bbtc_status run_count(bbtc_graph *g, const Plan &pl, const CountOutputs &out,
-                      uint32_t timeout_ms, cudaStream_t s, cudaEvent_t ev_begin,
-                      cudaEvent_t ev_end);
+// Occupancy of the counting kernel (set at plan time so that a count only
+// enqueues work).
+bbtc_status configure_count_kernels(Plan *pl);
+
+// a9-a10: per-task counts (plan scratch, Alg. 4 order), optional per-vertex
+// counts by position (vertex_count, device, n) and per-graph counts (plan
+// scratch); the total goes to the plan scratch. Enqueues only.
+bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
+                      bool per_graph, uint32_t timeout_ms, cudaStream_t s,
+                      cudaEvent_t ev_begin, cudaEvent_t ev_end);
 
 // Work figures of the oriented graph (device): sum_{(u,v)} d+(v) and
 // sum_u d+(u)(d+(u)-1)/2.
 bbtc_status wedge_sums(const bbtc_graph *g, uint64_t *in_sum, uint64_t *out_sum,
                        cudaStream_t s);
+
+// Gathers handles into one union handle (positions of handle h offset by the
+// vertices of the handles before it, graph-of-position filled); used by
+// bbtc_count_batch. The caller destroys the union.
+bbtc_status union_of(const bbtc_graph_t *gs, int32_t ng, cudaStream_t s, bbtc_graph **out);
 
 // Default p when the caller passes 0 (Sec. 7.3: p near the average degree,
 // clamped for a single resident GPU).

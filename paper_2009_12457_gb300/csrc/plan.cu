@@ -181,6 +181,7 @@ void free_plan(Plan *pl, cudaStream_t s) {
   dfree(pl->est, s);
   dfree(pl->order, s);
   dfree(pl->items, s);
+  dfree(pl->scratch, s);
   *pl = Plan();
 }
 
@@ -194,16 +195,15 @@ int default_p(const bbtc_graph *g) {
   return 8;
 }
 
-bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold,
+bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold, int chunk_req,
                        cudaStream_t s) {
-  if (g->plan.p == p && g->plan.kernel_mode == kernel_mode &&
-      g->plan.hash_threshold == hash_threshold)
-    return BBTC_OK;
+  if (plan_matches(g->plan, p, kernel_mode, hash_threshold, chunk_req)) return BBTC_OK;
   free_plan(&g->plan, s);
   Plan pl;
   pl.p = p;
   pl.kernel_mode = kernel_mode;
   pl.hash_threshold = hash_threshold;
+  pl.chunk_req = chunk_req;
   pl.ntasks = (int64_t)p * (p + 1) * (p + 2) / 6;
   const int64_t n = g->n, m = g->m;
   const int nb = g->nb;
@@ -270,9 +270,12 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   PLAN_TRY(launch_status("build_plan"));
 
   // work items: about 64 per resident warp in total, 64..4096 in-edges each
-  const int64_t warps = (int64_t)num_sms() * 48;
+  // (or the caller's choice)
+  const int64_t warps = (int64_t)num_sms() * 24;
   int64_t chunk = (m * (int64_t)(p < 3 ? p : 3)) / (warps * 64);
   chunk = chunk < 64 ? 64 : (chunk > 4096 ? 4096 : chunk);
+  if (chunk_req > 0) chunk = chunk_req;
+  pl.chunk = chunk;
   uint64_t *first = nullptr;
   PLAN_TRY(scratch.get(&first, nt + 1));
   k_item_counts<<<grid_for(nt, 256, 4), 256, 0, s>>>(pl.order, pl.tasks, pl.boff, p, nt, chunk,
@@ -295,8 +298,12 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
                                                      pl.items);
     PLAN_TRY(launch_status("build_plan"));
   }
+  // counting scratch and kernel configuration, so that a count only enqueues
+  PLAN_TRY(dalloc_n(&pl.scratch, SCR_TASKS + nt + g->ng, s));
+  PLAN_TRY(configure_count_kernels(&pl));
 #undef PLAN_TRY
-  pl.bytes = (uint64_t)m * 12 + (uint64_t)nt * 24 + (uint64_t)pl.nitems * sizeof(WorkItem);
+  pl.bytes = (uint64_t)m * 12 + (uint64_t)nt * 24 + (uint64_t)pl.nitems * sizeof(WorkItem) +
+             (uint64_t)(SCR_TASKS + nt + g->ng) * 8;
   g->plan = pl;
   return BBTC_OK;
 }

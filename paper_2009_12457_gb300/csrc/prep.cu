@@ -24,15 +24,26 @@ __global__ void k_validate_rowptr(const int64_t *__restrict__ rowptr, int64_t n,
 }
 
 // a1: one 64-bit key (min << nb) | max per input entry joining two different
-// vertices; self-loops (and, for symmetric input, entries with u > v) become
-// the sentinel, which sorts last and is dropped by the unique step.
+// vertices. Self-loops (and, for symmetric input, entries with u > v) emit
+// nothing. Two passes over tiles of EK_TILE entries: count the keys of each
+// tile, then (after a scan of the counts) write them compacted. Thread t of a
+// tile owns entries [t*EK_ITEMS, (t+1)*EK_ITEMS) and walks their rows forward
+// from one binary search inside the tile's row window.
+constexpr int EK_ITEMS = EK_TILE / EK_NT;
+
+// For a batch (voff != nullptr), graph g owns rows [voff[g], voff[g+1]) and
+// its entries are local ids in [0, voff[g+1] - voff[g]), shifted by voff[g].
+template <bool WRITE>
 __global__ void __launch_bounds__(EK_NT) k_emit_keys(const int64_t *__restrict__ rowptr,
                                                      const int32_t *__restrict__ colidx,
                                                      int64_t n, int64_t nnz, int nb,
-                                                     bool symmetric, uint64_t sentinel,
+                                                     bool symmetric,
+                                                     const int64_t *__restrict__ voff, int ng,
+                                                     uint64_t *__restrict__ tile_count,
                                                      uint64_t *__restrict__ keys,
                                                      int32_t *__restrict__ err) {
   __shared__ int64_t win[2];
+  __shared__ uint64_t tmp[EK_NT / 32 + 1];
   const int64_t ntiles = (nnz + EK_TILE - 1) / EK_TILE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t t0 = tile * EK_TILE;
@@ -49,24 +60,65 @@ __global__ void __launch_bounds__(EK_NT) k_emit_keys(const int64_t *__restrict__
     }
     __syncthreads();
     const int64_t rlo = win[0], rhi = win[1];
-    for (int64_t idx = t0 + threadIdx.x; idx < t1; idx += EK_NT) {
+    const int64_t first = t0 + (int64_t)threadIdx.x * EK_ITEMS;
+    uint64_t key[EK_ITEMS];
+    uint64_t c = 0;
+    int64_t u = rlo;
+    if (first < t1) {
       int64_t lo = rlo, hi = rhi + 1;
       while (hi - lo > 1) {
         int64_t mid = (lo + hi) >> 1;
-        if (rowptr[mid] <= idx) lo = mid; else hi = mid;
+        if (rowptr[mid] <= first) lo = mid; else hi = mid;
       }
-      const int64_t u = lo;
-      const int64_t v = colidx[idx];
-      uint64_t key = sentinel;
-      if (v < 0 || v >= n) {
-        atomicOr(err, 2);
-      } else if (v != u && !(symmetric && u > v)) {
-        uint64_t a = (uint64_t)(u < v ? u : v), b = (uint64_t)(u < v ? v : u);
-        key = (a << nb) | b;
-      }
-      keys[idx] = key;
+      u = lo;
     }
-    __syncthreads();
+    int gi = 0;
+    int64_t gbase = 0, gend = n;
+    if (voff) {
+      int lo = 0, hi = ng;  // last graph with voff[lo] <= u
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (voff[mid] <= u) lo = mid; else hi = mid;
+      }
+      gi = lo;
+      gbase = voff[gi];
+      gend = voff[gi + 1];
+    }
+#pragma unroll
+    for (int i = 0; i < EK_ITEMS; ++i) {
+      const int64_t idx = first + i;
+      key[i] = ~0ull;
+      if (idx < t1) {
+        while (u < rhi && rowptr[u + 1] <= idx) ++u;
+        if (voff) {
+          while (u >= gend && gi + 1 < ng) {
+            ++gi;
+            gbase = voff[gi];
+            gend = voff[gi + 1];
+          }
+        }
+        int64_t v = colidx[idx];
+        const bool in_range = voff ? (v >= 0 && v < gend - gbase) : (v >= 0 && v < n);
+        v += gbase;
+        if (!in_range) {
+          if (!WRITE) atomicOr(err, 2);
+        } else if (v != u && !(symmetric && u > v)) {
+          uint64_t a = (uint64_t)(u < v ? u : v), b = (uint64_t)(u < v ? v : u);
+          key[i] = (a << nb) | b;
+          ++c;
+        }
+      }
+    }
+    uint64_t total;
+    uint64_t pos = block_exclusive_scan<uint64_t, EK_NT>(c, tmp, &total);
+    if (!WRITE) {
+      if (threadIdx.x == 0) tile_count[tile] = total;
+    } else {
+      pos += tile_count[tile];
+#pragma unroll
+      for (int i = 0; i < EK_ITEMS; ++i)
+        if (key[i] != ~0ull) keys[pos++] = key[i];
+    }
   }
 }
 
@@ -93,7 +145,9 @@ __global__ void __launch_bounds__(UQ_NT) k_unique_count(const uint64_t *__restri
   if (threadIdx.x == 0) block_counts[blockIdx.x] = total;
 }
 
-// a1 + a2: compact the distinct keys and count each endpoint's degree.
+// a1 + a2: compact the distinct keys and count each endpoint's degree. Keys
+// are sorted by their first endpoint, so lanes holding equal endpoints add
+// once per group (match_any) instead of once per edge.
 __global__ void __launch_bounds__(UQ_NT) k_unique_write(const uint64_t *__restrict__ keys,
                                                         int64_t count, uint64_t sentinel,
                                                         const uint64_t *__restrict__ block_off,
@@ -101,6 +155,7 @@ __global__ void __launch_bounds__(UQ_NT) k_unique_write(const uint64_t *__restri
                                                         int32_t *__restrict__ deg) {
   __shared__ uint64_t tmp[UQ_NT / 32 + 1];
   const int64_t base = (int64_t)blockIdx.x * UQ_TILE + (int64_t)threadIdx.x * UQ_ITEMS;
+  const unsigned lane = threadIdx.x & 31u;
   bool head[UQ_ITEMS];
   uint64_t c = 0;
 #pragma unroll
@@ -113,12 +168,14 @@ __global__ void __launch_bounds__(UQ_NT) k_unique_write(const uint64_t *__restri
   const uint64_t mask = (1ull << nb) - 1ull;
 #pragma unroll
   for (int i = 0; i < UQ_ITEMS; ++i) {
-    if (head[i]) {
-      uint64_t k = keys[base + i];
-      ukeys[pos++] = k;
-      atomicAdd(&deg[k >> nb], 1);
-      atomicAdd(&deg[k & mask], 1);
-    }
+    uint64_t k = head[i] ? keys[base + i] : 0;
+    if (head[i]) ukeys[pos++] = k;
+    const int64_t a = head[i] ? (int64_t)(k >> nb) : -1;
+    const int64_t b = head[i] ? (int64_t)(k & mask) : -1;
+    unsigned peers = __match_any_sync(0xffffffffu, a);
+    if (a >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&deg[a], __popc(peers));
+    peers = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&deg[b], __popc(peers));
   }
 }
 
@@ -138,6 +195,22 @@ __global__ void k_rank_finish(const uint64_t *__restrict__ sorted, int64_t n, in
     int32_t v = (int32_t)(sorted[r] & mask);
     perm[r] = v;
     rank[v] = (int32_t)r;
+  }
+}
+
+// Batch handles: graph of each position (the graph owning perm[r]).
+__global__ void k_graph_of_position(const int32_t *__restrict__ perm, int64_t n,
+                                    const int64_t *__restrict__ voff, int ng,
+                                    int32_t *__restrict__ gid) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = perm[r];
+    int lo = 0, hi = ng;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (voff[mid] <= v) lo = mid; else hi = mid;
+    }
+    gid[r] = lo;
   }
 }
 
@@ -199,30 +272,55 @@ bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t 
     BBTC_LAUNCH_CHECK();
   }
 
-  // ---- a1: canonical keys, sort, unique; a2: degree
+  // ---- a1: canonical keys (compacted), sort, unique; a2: degree
+  // (no key equals the all-ones value: it would need min == max)
   const uint64_t sentinel = (nb * 2 >= 64) ? ~0ull : ((1ull << (2 * nb)) - 1ull);
   uint64_t *ka = nullptr, *kb = nullptr;
-  const int64_t kcap = nnz > n ? nnz : n;  // buffers are reused for the n rank keys
-  BBTC_TRY(scratch.get(&ka, kcap));
-  BBTC_TRY(scratch.get(&kb, kcap));
+  int64_t nkeys = 0;
   if (nnz > 0) {
-    k_emit_keys<<<grid_for((nnz + EK_TILE - 1) / EK_TILE, 1, 64), EK_NT, 0, s>>>(
-        d_rowptr, d_colidx, n, nnz, nb, symmetric, sentinel, ka, err);
+    const int64_t ntiles = (nnz + EK_TILE - 1) / EK_TILE;
+    uint64_t *tile_count = nullptr;
+    BBTC_TRY(scratch.get(&tile_count, ntiles + 1));
+    const unsigned grid = grid_for(ntiles, 1, 64);
+    k_emit_keys<false><<<grid, EK_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, nb, symmetric,
+                                               g->voff, g->ng, tile_count, nullptr, err);
     BBTC_LAUNCH_CHECK();
-  }
-  int32_t herr = 0;
-  BBTC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  BBTC_CUDA(cudaStreamSynchronize(s));
-  if (herr & 1) {
-    set_error("bbtc_graph_create: rowptr[0] != 0 or rowptr decreases");
-    return BBTC_EINVAL;
-  }
-  if (herr & 2) {
-    set_error("bbtc_graph_create: colidx entry outside [0, n)");
-    return BBTC_EINVAL;
+    BBTC_TRY(exclusive_scan_u64(tile_count, tile_count, ntiles + 1, s));
+    BBTC_CUDA(cudaMemcpyAsync(&hstats[0], &tile_count[ntiles], sizeof(int64_t),
+                              cudaMemcpyDeviceToDevice, s));
+    int64_t h[1] = {0};
+    int32_t herr = 0;
+    BBTC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BBTC_CUDA(cudaMemcpyAsync(h, &hstats[0], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BBTC_CUDA(cudaStreamSynchronize(s));
+    if (herr & 1) {
+      set_error("bbtc_graph_create: rowptr[0] != 0 or rowptr decreases");
+      return BBTC_EINVAL;
+    }
+    if (herr & 2) {
+      set_error("bbtc_graph_create: colidx entry outside [0, n)");
+      return BBTC_EINVAL;
+    }
+    nkeys = h[0];
+    const int64_t kcap = nkeys > n ? nkeys : n;  // the buffers also take the n rank keys
+    BBTC_TRY(scratch.get(&ka, kcap));
+    BBTC_TRY(scratch.get(&kb, kcap));
+    k_emit_keys<true><<<grid, EK_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, nb, symmetric,
+                                              g->voff, g->ng, tile_count, ka, err);
+    BBTC_LAUNCH_CHECK();
+  } else {
+    int32_t herr = 0;
+    BBTC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BBTC_CUDA(cudaStreamSynchronize(s));
+    if (herr & 1) {
+      set_error("bbtc_graph_create: rowptr[0] != 0 or rowptr decreases");
+      return BBTC_EINVAL;
+    }
+    BBTC_TRY(scratch.get(&ka, n));
+    BBTC_TRY(scratch.get(&kb, n));
   }
   bool in_alt = false;
-  BBTC_TRY(radix_sort(ka, kb, nullptr, nullptr, nnz, 0, 2 * nb, s, &in_alt));
+  BBTC_TRY(radix_sort(ka, kb, nullptr, nullptr, nkeys, 0, 2 * nb, s, &in_alt));
   uint64_t *sorted = in_alt ? kb : ka;
   uint64_t *ukeys = in_alt ? ka : kb;
 
@@ -230,14 +328,14 @@ bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t 
   g->bytes += (uint64_t)(n > 0 ? n : 1) * sizeof(int32_t);
   BBTC_CUDA(cudaMemsetAsync(g->deg, 0, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s));
   int64_t m = 0;
-  if (nnz > 0) {
-    const int64_t nblk = (nnz + UQ_TILE - 1) / UQ_TILE;
+  if (nkeys > 0) {
+    const int64_t nblk = (nkeys + UQ_TILE - 1) / UQ_TILE;
     uint64_t *boff = nullptr;
     BBTC_TRY(scratch.get(&boff, nblk + 1));
-    k_unique_count<<<(unsigned)nblk, UQ_NT, 0, s>>>(sorted, nnz, sentinel, boff);
+    k_unique_count<<<(unsigned)nblk, UQ_NT, 0, s>>>(sorted, nkeys, sentinel, boff);
     BBTC_LAUNCH_CHECK();
     BBTC_TRY(exclusive_scan_u64(boff, boff, nblk + 1, s));  // boff[nblk] = total
-    k_unique_write<<<(unsigned)nblk, UQ_NT, 0, s>>>(sorted, nnz, sentinel, boff, nb, ukeys,
+    k_unique_write<<<(unsigned)nblk, UQ_NT, 0, s>>>(sorted, nkeys, sentinel, boff, nb, ukeys,
                                                      g->deg);
     BBTC_LAUNCH_CHECK();
     BBTC_CUDA(cudaMemcpyAsync(&hstats[0], &boff[nblk], sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
@@ -278,6 +376,13 @@ bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t 
     k_rank_finish<<<grid_for(n, 256, 16), 256, 0, s>>>(in_alt ? rk_alt : rk, n, nb, g->perm,
                                                         rank);
     BBTC_LAUNCH_CHECK();
+    if (g->voff) {
+      BBTC_TRY(dalloc_n(&g->gid, n, s));
+      g->bytes += (uint64_t)n * sizeof(int32_t);
+      k_graph_of_position<<<grid_for(n, 256, 16), 256, 0, s>>>(g->perm, n, g->voff, g->ng,
+                                                              g->gid);
+      BBTC_LAUNCH_CHECK();
+    }
   }
 
   // ---- a4: orient and build the oriented CSR

@@ -1,0 +1,72 @@
+"""Serving loop: each request's count is the same alone and in the mix (GPU)."""
+import numpy as np
+import pytest
+
+import graphgen
+import paper_2009_12457_gb300 as bb
+from paper_2009_12457_gb300 import serve
+from paper_2009_12457_gb300.autotune import Autotuner
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+def request_key(rid, scales=(8, 9, 10, 11, 12, 13), seeds=6):
+    """Scale and graph seed of request rid, from the counter-based draw of its id."""
+    d = graphgen.draw(5, 9, rid)
+    return (scales[d % len(scales)], (d >> 32) % seeds)
+
+
+_SOURCE_CACHE = {}
+
+
+def source(key):
+    if key not in _SOURCE_CACHE:
+        scale, seed = key
+        _SOURCE_CACHE[key] = graphgen.rmat(scale, 16, 1000 + seed)
+    return _SOURCE_CACHE[key]
+
+
+def test_served_counts_equal_counts_alone():
+    arrivals = serve.poisson_trace(400.0, 1.5, seed=5)
+    keys = [request_key(i) for i in range(len(arrivals))]
+    alone = {}
+    for k in set(keys):
+        with bb.Graph(*source(k)) as g:
+            alone[k] = g.count(p=2)
+    # a budget of a few graphs forces admission waits and evictions
+    srv = serve.Server(source, device_budget_bytes=12 << 20, max_batch=32, workers=2, p=2)
+    try:
+        reqs = serve.run_open_loop(srv, keys, arrivals)
+    finally:
+        srv.close()
+    assert len(reqs) == len(keys)
+    assert all(r.status == 0 for r in reqs)
+    assert all(r.count == alone[r.key] for r in reqs)
+    assert srv.evictions > 0 and srv.hits > 0
+    assert max(r.batch_size for r in reqs) > 1  # requests really shared launches
+    summary = serve.latency_summary(reqs)
+    assert summary["p99_ms"] >= summary["p50_ms"] > 0
+
+
+def test_serial_baseline_matches():
+    keys = [request_key(i) for i in range(12)]
+    counts, rate = serve.serial_baseline(source, keys, p=2)
+    for k, c in zip(keys, counts):
+        with bb.Graph(*source(k)) as g:
+            assert c == g.count(p=3)
+    assert rate > 0
+
+
+def test_autotuner_choice_gives_the_same_count(tmp_path):
+    n, rp, ci = graphgen.rmat(14, 16, 3)
+    tuner = Autotuner(cache_path=str(tmp_path / "tune.json"), repeats=1)
+    with bb.Graph(n, rp, ci) as g:
+        ref = g.count(p=1)
+        choice = tuner.tune(g, p_choices=(1, 2, 4))
+        assert choice["p"] in (1, 2, 4) and choice["count_ms"] > 0
+        assert bb.bbtc_count(g.handle, Autotuner.opts(choice)) == ref
+    again = Autotuner(cache_path=str(tmp_path / "tune.json"))
+    with bb.Graph(n, rp, ci) as g:
+        assert again.choice(g, tune_if_missing=False)["p"] == choice["p"]
