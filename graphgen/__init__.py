@@ -68,6 +68,7 @@ def _load():
         lib.gg_chunglu_pairs.argtypes = [i64, i64, P, P, u64, P, P]
         lib.gg_pairs_to_csr.argtypes = [i64, i64, P, P, P, P]
         lib.gg_num_threads.restype = ctypes.c_int
+        lib.gg_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
         return lib
 
@@ -194,3 +195,19 @@ def batch_graph(g: int):
     if s["kind"] == "gnm":
         return gnm(s["n"], s["pairs"], s["seed"])
     return rmat(s["scale"], s["edge_factor"], s["seed"])
+
+
+def batch_graphs(count: int = 4096, workers: int | None = None):
+    """The batched workload's graphs 0..count-1 (see batch_spec), generated by a
+    pool of host threads with one OpenMP thread each (the result does not depend
+    on either)."""
+    import concurrent.futures
+    workers = workers or max(1, os.cpu_count() or 1)
+    lib = _load()
+
+    def one(g):
+        lib.gg_set_threads(1)
+        return batch_graph(g)
+
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(one, range(count)))

@@ -204,6 +204,15 @@ void gg_pairs_to_csr(int64_t n, int64_t M, const int32_t *src, const int32_t *ds
   }
 }
 
+/* OpenMP threads used by the calling thread's later generator calls. */
+void gg_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 int gg_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

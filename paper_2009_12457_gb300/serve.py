@@ -40,13 +40,16 @@ class Request:
 
 
 class _Entry:
-    __slots__ = ("handle", "bytes", "refs", "ready")
+    __slots__ = ("handle", "bytes", "refs", "ready", "lock")
 
     def __init__(self):
         self.handle = 0
         self.bytes = 0
         self.refs = 0
         self.ready = threading.Event()
+        # a handle is not thread-safe: a direct count (which builds and uses
+        # the handle's plan) holds this lock; batch counts only read the handle
+        self.lock = threading.Lock()
 
 
 class Server:
@@ -160,7 +163,9 @@ class Server:
                     handles = [self.cache[k].handle for k in acquired]
                     opts = make_opts(p=self.p, kernel=self.kernel, stream=stream)
                     if len(handles) == 1:
-                        counts = np.array([bbtc_count(handles[0], opts)], dtype=np.uint64)
+                        with self.cache[acquired[0]].lock:
+                            c = bbtc_count(handles[0], opts)
+                        counts = np.array([c], dtype=np.uint64)
                         stats = np.zeros(1, dtype=np.int32)
                     else:
                         counts, stats = bbtc_count_batch(handles, opts)
