@@ -22,14 +22,7 @@ constexpr int CT_NT = 256;
 constexpr int MAXP = 64;
 
 struct CountParams {
-  const int64_t *rowptr;
-  const int32_t *colidx;
-  const int32_t *ie_u;
-  const int32_t *ie_v;
-  const uint32_t *ie_e;
-  const int32_t *cuts;
-  int p;
-  const int32_t *tasks;
+  const TaskDesc *desc;  // per task (Alg. 4 order): where its three blocks live
   const WorkItem *items;
   int64_t nitems;
   unsigned long long *head;
@@ -58,26 +51,28 @@ __device__ __forceinline__ uint32_t hash_slot(int32_t w, int log2h) {
   return ((uint32_t)w * 2654435761u) >> (32 - log2h);
 }
 
-// Membership of w in the sorted list stage[0, len).
+// Membership of w in the sorted list stage[0, len): lower bound by a fixed
+// number of halvings (the same for every lane, since len is warp-uniform).
 __device__ __forceinline__ bool sorted_contains(const int32_t *stage, int len, int32_t w) {
-  int lo = 0, hi = len;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (stage[mid] < w) lo = mid + 1; else hi = mid;
-  }
-  return lo < len && stage[lo] == w;
+  int pos = 0;
+  for (int step = len > 0 ? 1 << (31 - __clz(len)) : 0; step > 0; step >>= 1)
+    if (pos + step <= len && stage[pos + step - 1] < w) pos += step;
+  return pos < len && stage[pos] == w;
 }
 
-// Membership of w in the open-addressed table stage[0, 2^log2h) (linear probing;
-// the table is at most half full, so an empty slot ends every probe sequence).
+// Membership of w in the open-addressed table stage[0, 2^log2h) (linear
+// probing, at most half full). The probe reads four slots per 16-byte load,
+// starting at the 4-slot group of w's hash slot, so nearly every lookup ends
+// after one load and the lanes of a warp stay together.
 __device__ __forceinline__ bool hash_contains(const int32_t *stage, int log2h, int32_t w) {
-  const uint32_t mask = (1u << log2h) - 1u;
-  uint32_t h = hash_slot(w, log2h);
-  for (uint32_t n = 0; n <= mask; ++n) {
-    const int32_t s = stage[h];
-    if (s == w) return true;
-    if (s == EMPTY) return false;
-    h = (h + 1) & mask;
+  const uint32_t gmask = (1u << (log2h - 2)) - 1u;
+  uint32_t g = hash_slot(w, log2h) >> 2;
+  const int4 *groups = reinterpret_cast<const int4 *>(stage);
+  for (uint32_t n = 0; n <= gmask; ++n) {
+    const int4 q = groups[g];
+    if (q.x == w || q.y == w || q.z == w || q.w == w) return true;
+    if (q.x == EMPTY || q.y == EMPTY || q.z == EMPTY || q.w == EMPTY) return false;
+    g = (g + 1) & gmask;
   }
   return false;
 }
@@ -100,18 +95,12 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
   constexpr bool PER_VERTEX = (MODE & MODE_VERTEX) != 0;
   constexpr bool PER_GRAPH = (MODE & MODE_GRAPH) != 0;
   extern __shared__ __align__(16) unsigned char count_smem_raw[];
-  __shared__ int32_t cuts[MAXP + 1];
-  for (int i = threadIdx.x; i <= P.p; i += CT_NT) cuts[i] = P.cuts[i];
-  __syncthreads();
   const unsigned lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
   int32_t *stage = reinterpret_cast<int32_t *>(count_smem_raw) + warp * STAGE;
   LaneRec &rec = reinterpret_cast<LaneRec *>(count_smem_raw + (size_t)(CT_NT / 32) * STAGE *
                                                                   sizeof(int32_t))[warp];
   const uint64_t t_start = P.timeout_ns ? global_ns() : 0;
-  const int64_t *__restrict__ rowptr = P.rowptr;
-  const int32_t *__restrict__ col = P.colidx;
-  const unsigned lt_mask = (1u << lane) - 1u;
   // (task, v) whose N(G_jk, v) is in `stage`, and how it is stored
   unsigned long long staged_tag = ~0ull;
   int staged_len = 0, staged_log2h = 0;
@@ -129,17 +118,23 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
     const WorkItem w = P.items[it];
     const int t = w.task;
     const bool use_hash = (w.flags & 1) != 0;
-    const int j = P.tasks[3 * t + 1], k = P.tasks[3 * t + 2];
-    const int32_t ck = cuts[k], ck1 = cuts[k + 1];
-    const bool diag = k == j;          // N(G_jk, v) starts at N(v)'s start
-    const bool last = k == P.p - 1;    // partial lists run to the row's end
+    const TaskDesc &d = P.desc[t];
+    const int32_t *__restrict__ ie_u = d.ie_u - d.ie_off;
+    const int32_t *__restrict__ ie_v = d.ie_v - d.ie_off;
+    const uint32_t *__restrict__ ie_e = d.ie_e - d.ie_off;
+    const uint32_t *__restrict__ rp_ik = d.rp_ik;
+    const uint32_t *__restrict__ rp_jk = d.rp_jk;
+    const int32_t *__restrict__ ci_ik = d.ci_ik - d.ci_ik_off;  // indexed by position
+    const int32_t *__restrict__ ci_jk = d.ci_jk - d.ci_jk_off;
+    const int32_t c_i = d.c_i, c_j = d.c_j;
+    const bool diag = d.diag != 0;
     unsigned long long acc = 0;
 
     int64_t base = w.x0;
     while (base < w.x1) {
       const int64_t x = base + lane;
       const bool valid = x < w.x1;
-      const int32_t v = valid ? P.ie_v[x] : -1;
+      const int32_t v = valid ? ie_v[x] : -1;
       // in-edges are sorted by destination: lanes equal to lane 0's v form a prefix
       const int32_t v0 = __shfl_sync(0xffffffffu, v, 0);
       const unsigned eq = __ballot_sync(0xffffffffu, valid && v == v0);
@@ -163,29 +158,28 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
       int32_t u = 0;
       int64_t e = 0;
       if (active) {
-        u = P.ie_u[x];
-        e = P.ie_e[x];
+        u = ie_u[x];
+        e = ie_e[x];
       }
+      // N(G_jk, v): direct row pointers of block (j, k)
       int64_t b0 = 0, b1 = 0;
       if (uniform) {
         if (lane == 0) {
-          const int64_t rv0 = rowptr[v0], rv1 = rowptr[v0 + 1];
-          b0 = diag ? rv0 : lower_bound_dev<int32_t, int64_t>(col, rv0, rv1, ck);
-          b1 = last ? rv1 : lower_bound_dev<int32_t, int64_t>(col, b0, rv1, ck1);
+          b0 = rp_jk[v0 - c_j];
+          b1 = rp_jk[v0 - c_j + 1];
         }
         b0 = __shfl_sync(0xffffffffu, b0, 0);
         b1 = __shfl_sync(0xffffffffu, b1, 0);
       } else if (active) {
-        const int64_t rv0 = rowptr[v], rv1 = rowptr[v + 1];
-        b0 = diag ? rv0 : lower_bound_dev<int32_t, int64_t>(col, rv0, rv1, ck);
-        b1 = last ? rv1 : lower_bound_dev<int32_t, int64_t>(col, b0, rv1, ck1);
+        b0 = rp_jk[v - c_j];
+        b1 = rp_jk[v - c_j + 1];
       }
-      // N(G_ik, u) restricted to entries above v
+      // N(G_ik, u) restricted to entries above v (for k == j, the entries of
+      // G_ij after (u, v) itself)
       int64_t s0 = 0, s1 = 0;
       if (active && b1 > b0) {
-        const int64_t ru1 = rowptr[u + 1];
-        s0 = diag ? e + 1 : lower_bound_dev<int32_t, int64_t>(col, rowptr[u], ru1, ck);
-        s1 = last ? ru1 : lower_bound_dev<int32_t, int64_t>(col, s0, ru1, ck1);
+        s1 = rp_ik[u - c_i + 1];
+        s0 = diag ? e + 1 : rp_ik[u - c_i];
       }
       const uint32_t len = (uint32_t)(s1 - s0);
       const uint32_t incl = warp_inclusive_scan(len);
@@ -213,8 +207,10 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
             __syncwarp();
             const uint32_t hmask = (uint32_t)hsize - 1u;
             for (int i = lane; i < blen; i += 32) {
-              const int32_t key = col[b0 + i];
-              uint32_t h = hash_slot(key, log2h);
+              const int32_t key = ci_jk[b0 + i];
+              // linear probing from the first slot of the key's 4-slot group,
+              // the order in which hash_contains reads the table
+              uint32_t h = hash_slot(key, log2h) & ~3u;
               for (int n = 0; n < hsize; ++n) {
                 if (atomicCAS(&stage[h], EMPTY, key) == EMPTY) break;
                 h = (h + 1) & hmask;
@@ -222,7 +218,7 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
             }
             staged_log2h = log2h;
           } else {
-            for (int i = lane; i < blen; i += 32) stage[i] = col[b0 + i];
+            for (int i = lane; i < blen; i += 32) stage[i] = ci_jk[b0 + i];
           }
           __syncwarp();
           staged_tag = tag;
@@ -266,14 +262,14 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
             hi = rec.b1[o];
           }
         }
-        const int32_t wv = col[addr + q];
+        const int32_t wv = ci_ik[addr + q];
         bool hit;
         if (staged) {
           hit = staged_hash ? hash_contains(stage, staged_log2h, wv)
                             : sorted_contains(stage, staged_len, wv);
         } else {
-          const int64_t pos = lower_bound_dev<int32_t, int64_t>(col, lo, hi, wv);
-          hit = pos < hi && col[pos] == wv;
+          const int64_t pos = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, wv);
+          hit = pos < hi && ci_jk[pos] == wv;
         }
         if (hit) {
           ++acc;
@@ -390,14 +386,7 @@ bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_
   if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
   if (pl.nitems > 0) {
     CountParams P;
-    P.rowptr = g->rowptr;
-    P.colidx = g->colidx;
-    P.ie_u = pl.ie_u;
-    P.ie_v = pl.ie_v;
-    P.ie_e = pl.ie_e;
-    P.cuts = pl.cuts;
-    P.p = pl.p;
-    P.tasks = pl.tasks;
+    P.desc = pl.desc;
     P.items = pl.items;
     P.nitems = pl.nitems;
     P.head = scr + SCR_HEAD;
@@ -509,14 +498,7 @@ extern "C" bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *c
     }
     if (pl.nitems > 0) {
       CountParams P;
-      P.rowptr = g->rowptr;
-      P.colidx = g->colidx;
-      P.ie_u = pl.ie_u;
-      P.ie_v = pl.ie_v;
-      P.ie_e = pl.ie_e;
-      P.cuts = pl.cuts;
-      P.p = pl.p;
-      P.tasks = pl.tasks;
+      P.desc = pl.desc;
       P.items = pl.items;
       P.nitems = pl.nitems;
       P.head = scratch + NOALLOC_HEAD;

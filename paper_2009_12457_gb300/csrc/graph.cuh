@@ -5,6 +5,30 @@
 
 namespace bbtc {
 
+// Where the counting kernel finds the three blocks of task t = (i, j, k):
+//  - the in-edges of G_ij (source u, destination v, position of (u,v) among
+//    G_ij's columns), grouped by v: element x of the task's range lives at
+//    ie_*[x - ie_off];
+//  - N(G_ik, u) for u in V_i: columns [rp_ik[u - c_i], rp_ik[u - c_i + 1]) of
+//    ci_ik, where column position q lives at ci_ik[q - ci_ik_off];
+//  - N(G_jk, v) for v in V_j: likewise through rp_jk / ci_jk.
+// For k == j, G_ik is G_ij and the in-edge position indexes it directly.
+struct TaskDesc {
+  const int32_t *ie_u;
+  const int32_t *ie_v;
+  const uint32_t *ie_e;
+  int64_t ie_off;
+  const uint32_t *rp_ik;
+  const int32_t *ci_ik;
+  int64_t ci_ik_off;
+  const uint32_t *rp_jk;
+  const int32_t *ci_jk;
+  int64_t ci_jk_off;
+  int32_t c_i, c_j;
+  int32_t diag;  // k == j
+  int32_t task;  // index in Alg. 4 order
+};
+
 // One unit of counting work: the in-edges [x0, x1) of block G_ij (grouped by
 // destination v) for task t = (i, j, k).
 struct WorkItem {
@@ -19,9 +43,18 @@ struct Plan {
   int p = 0;
   int64_t ntasks = 0;
   int32_t *cuts = nullptr;      // p+1
+  int32_t h_cuts[65] = {0};     // host copy of the cuts
+  // physical block CSR (Sec. 4.1, BCSR): blocks (a, b), a <= b, in row-major
+  // order; block (a, b)'s row pointers are rp[rpb[a*p+b] .. + |V_a|] and hold
+  // positions in ci, the block-major concatenation of all blocks' columns
+  uint32_t *rp = nullptr;
+  int32_t *ci = nullptr;
+  int64_t h_rpb[64 * 64] = {0};
+  int64_t total_rp = 0;
+  TaskDesc *desc = nullptr;     // T, in Alg. 4 order
   int32_t *ie_u = nullptr;      // m: in-edges sorted by (part(u), v, u): source u
   int32_t *ie_v = nullptr;      // m: destination v
-  uint32_t *ie_e = nullptr;     // m: position of the edge (u,v) in the oriented CSR
+  uint32_t *ie_e = nullptr;     // m: position of the edge (u,v) in ci
   int64_t *boff = nullptr;      // p*(p+1): block (i,j) in-edges = [boff[i*(p+1)+j], +1)
   int32_t *tasks = nullptr;     // 3*T: (i,j,k) in Alg. 4 order
   double *est = nullptr;        // T: ExecTime in Alg. 4 order

@@ -7,6 +7,8 @@
 //   a7 task composition: all (i,j,k), i <= j <= k (Sec. 4.2, Alg. 4)
 //   a8 ExecTime estimate and non-increasing order (Sec. 5), split into work
 //      items of at most `chunk` in-edges each
+#include <new>
+
 #include "graph.cuh"
 #include "primitives.cuh"
 
@@ -50,17 +52,83 @@ __global__ void k_inedge_keys(const int32_t *__restrict__ colidx,
   }
 }
 
+// In-edges from the sorted keys; the edge's position becomes its position in
+// the block-major column array (pos_of_edge).
 __global__ void k_inedge_finish(const uint64_t *__restrict__ keys,
                                 const uint32_t *__restrict__ vals, int64_t m, int nb,
-                                const int32_t *__restrict__ esrc, int32_t *__restrict__ ie_u,
-                                int32_t *__restrict__ ie_v, uint32_t *__restrict__ ie_e) {
+                                const int32_t *__restrict__ esrc,
+                                const uint32_t *__restrict__ pos_of_edge,
+                                int32_t *__restrict__ ie_u, int32_t *__restrict__ ie_v,
+                                uint32_t *__restrict__ ie_e) {
   const uint64_t mask = (1ull << nb) - 1ull;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m;
        x += (int64_t)gridDim.x * blockDim.x) {
     uint32_t e = vals[x];
     ie_v[x] = (int32_t)(keys[x] & mask);
-    ie_e[x] = e;
+    ie_e[x] = pos_of_edge[e];
     ie_u[x] = esrc[e];
+  }
+}
+
+// BCSR, step 1: for every (block (a,b), row x of V_a) the number of entries of
+// row c_a + x in V_b and where they start in the oriented CSR. The trailing
+// slot of each block's segment counts 0 (it becomes the block's end).
+__global__ void k_bcsr_count(const int64_t *__restrict__ rowptr,
+                             const int32_t *__restrict__ colidx,
+                             const int32_t *__restrict__ cuts_g, int p, int nblk,
+                             const int64_t *__restrict__ seg_g, const int32_t *__restrict__ blk_g,
+                             int64_t total, uint64_t *__restrict__ cnt,
+                             uint32_t *__restrict__ start) {
+  __shared__ int32_t cuts[MAXP + 1];
+  __shared__ int64_t seg[MAXP * (MAXP + 1) / 2 + 1];
+  __shared__ int32_t blk[MAXP * (MAXP + 1) / 2];
+  for (int i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
+  for (int i = threadIdx.x; i <= nblk; i += blockDim.x) seg[i] = seg_g[i];
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) blk[i] = blk_g[i];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nblk;  // last block whose segment starts at or before i
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (seg[mid] <= i) lo = mid; else hi = mid;
+    }
+    const int a = blk[lo] >> 8, b = blk[lo] & 0xff;
+    const int64_t x = i - seg[lo];
+    uint64_t c = 0;
+    uint32_t st = 0;
+    if (x < (int64_t)(cuts[a + 1] - cuts[a])) {
+      const int64_t u = cuts[a] + x;
+      const int64_t rs = rowptr[u], re = rowptr[u + 1];
+      // entries of row u are above u >= c_a, so those in V_a start the row
+      const int64_t S = b == a ? rs : lower_bound_dev<int32_t, int64_t>(colidx, rs, re, cuts[b]);
+      const int64_t E = b == p - 1 ? re : lower_bound_dev<int32_t, int64_t>(colidx, S, re, cuts[b + 1]);
+      c = (uint64_t)(E - S);
+      st = (uint32_t)S;
+    }
+    cnt[i] = c;
+    start[i] = st;
+  }
+}
+
+// BCSR, step 2: copy each (row, block) run of columns to its block-major
+// position, record where every CSR edge went, and narrow the positions.
+__global__ void k_bcsr_fill(const int32_t *__restrict__ colidx, const uint64_t *__restrict__ pos,
+                            const uint32_t *__restrict__ start, int64_t total,
+                            int32_t *__restrict__ ci, uint32_t *__restrict__ pos_of_edge,
+                            uint32_t *__restrict__ rp) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t q0 = pos[i];
+    rp[i] = (uint32_t)q0;
+    if (i + 1 < total) {
+      const uint64_t len = pos[i + 1] - q0;
+      const uint32_t S = start[i];
+      for (uint64_t t = 0; t < len; ++t) {
+        ci[q0 + t] = colidx[S + t];
+        pos_of_edge[S + t] = (uint32_t)(q0 + t);
+      }
+    }
   }
 }
 
@@ -182,6 +250,9 @@ void free_plan(Plan *pl, cudaStream_t s) {
   dfree(pl->order, s);
   dfree(pl->items, s);
   dfree(pl->scratch, s);
+  dfree(pl->rp, s);
+  dfree(pl->ci, s);
+  dfree(pl->desc, s);
   *pl = Plan();
 }
 
@@ -223,7 +294,61 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   k_cuts<<<1, MAXP + 1, 0, s>>>(g->rowptr, n, p, pl.cuts);
   PLAN_TRY(launch_status("build_plan"));
 
-  // a6: in-edges grouped by (part(u), v, u) and the block offsets
+  // a6: physical blocks. Host table of blocks (a, b), a <= b, row-major, each
+  // with a row-pointer segment of |V_a| + 1 slots.
+  if (cudaMemcpyAsync(pl.h_cuts, pl.cuts, sizeof(int32_t) * (size_t)(p + 1),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("build_plan: reading the cuts failed");
+    free_plan(&pl, s);
+    return BBTC_ECUDA;
+  }
+  const int nblk = p * (p + 1) / 2;
+  int64_t h_seg[MAXP * (MAXP + 1) / 2 + 1];
+  int32_t h_blk[MAXP * (MAXP + 1) / 2];
+  {
+    int bi = 0;
+    int64_t off = 0;
+    for (int a = 0; a < p; ++a)
+      for (int b = a; b < p; ++b) {
+        h_seg[bi] = off;
+        h_blk[bi] = (a << 8) | b;
+        pl.h_rpb[a * p + b] = off;
+        off += (int64_t)(pl.h_cuts[a + 1] - pl.h_cuts[a]) + 1;
+        ++bi;
+      }
+    h_seg[nblk] = off;
+    pl.total_rp = off;
+  }
+  int64_t *d_seg = nullptr;
+  int32_t *d_blk = nullptr;
+  uint64_t *cnt = nullptr;
+  uint32_t *start = nullptr, *pos_of_edge = nullptr;
+  PLAN_TRY(scratch.get(&d_seg, nblk + 1));
+  PLAN_TRY(scratch.get(&d_blk, nblk));
+  PLAN_TRY(scratch.get(&cnt, pl.total_rp));
+  PLAN_TRY(scratch.get(&start, pl.total_rp));
+  PLAN_TRY(scratch.get(&pos_of_edge, m));
+  PLAN_TRY(dalloc_n(&pl.rp, pl.total_rp, s));
+  PLAN_TRY(dalloc_n(&pl.ci, m, s));
+  if (cudaMemcpyAsync(d_seg, h_seg, sizeof(int64_t) * (size_t)(nblk + 1), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess ||
+      cudaMemcpyAsync(d_blk, h_blk, sizeof(int32_t) * (size_t)nblk, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess) {
+    set_error("build_plan: copying the block table failed");
+    free_plan(&pl, s);
+    return BBTC_ECUDA;
+  }
+  k_bcsr_count<<<grid_for(pl.total_rp, 256, 32), 256, 0, s>>>(
+      g->rowptr, g->colidx, pl.cuts, p, nblk, d_seg, d_blk, pl.total_rp, cnt, start);
+  PLAN_TRY(launch_status("build_plan"));
+  PLAN_TRY(exclusive_scan_u64(cnt, cnt, pl.total_rp, s));
+  k_bcsr_fill<<<grid_for(pl.total_rp, 256, 32), 256, 0, s>>>(g->colidx, cnt, start,
+                                                              pl.total_rp, pl.ci, pos_of_edge,
+                                                              pl.rp);
+  PLAN_TRY(launch_status("build_plan"));
+
+  // in-edges grouped by (part(u), v, u), and the block offsets
   uint64_t *ka = nullptr, *kb = nullptr;
   uint32_t *va = nullptr, *vb = nullptr;
   PLAN_TRY(scratch.get(&ka, m));
@@ -242,7 +367,8 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
     PLAN_TRY(launch_status("build_plan"));
     PLAN_TRY(radix_sort(ka, kb, va, vb, m, 0, nb + pbits, s, &in_alt));
     k_inedge_finish<<<grid_for(m, 256, 32), 256, 0, s>>>(in_alt ? kb : ka, in_alt ? vb : va, m,
-                                                          nb, g->esrc, pl.ie_u, pl.ie_v, pl.ie_e);
+                                                          nb, g->esrc, pos_of_edge, pl.ie_u,
+                                                          pl.ie_v, pl.ie_e);
     PLAN_TRY(launch_status("build_plan"));
   }
   k_block_offsets<<<(p * (p + 1) + 127) / 128, 128, 0, s>>>(in_alt ? kb : ka, m, pl.cuts, p, nb,
@@ -268,6 +394,46 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   PLAN_TRY(radix_sort(okeys, okeys_alt, ovals, ovals_alt, nt, 0, 64, s, &in_alt));
   k_order_finish<<<grid_for(nt, 256, 4), 256, 0, s>>>(in_alt ? ovals_alt : ovals, nt, pl.order);
   PLAN_TRY(launch_status("build_plan"));
+
+  // task descriptors: every block of the resident BCSR
+  {
+    TaskDesc *h_desc = new (std::nothrow) TaskDesc[(size_t)nt];
+    if (!h_desc) {
+      set_error("build_plan: host allocation failed");
+      free_plan(&pl, s);
+      return BBTC_ENOMEM;
+    }
+    int64_t t = 0;
+    for (int i = 0; i < p; ++i)
+      for (int j = i; j < p; ++j)
+        for (int k = j; k < p; ++k, ++t) {
+          TaskDesc &d = h_desc[t];
+          d.ie_u = pl.ie_u;
+          d.ie_v = pl.ie_v;
+          d.ie_e = pl.ie_e;
+          d.ie_off = 0;
+          d.rp_ik = pl.rp + pl.h_rpb[i * p + k];
+          d.ci_ik = pl.ci;
+          d.ci_ik_off = 0;
+          d.rp_jk = pl.rp + pl.h_rpb[j * p + k];
+          d.ci_jk = pl.ci;
+          d.ci_jk_off = 0;
+          d.c_i = pl.h_cuts[i];
+          d.c_j = pl.h_cuts[j];
+          d.diag = k == j;
+          d.task = (int32_t)t;
+        }
+    bbtc_status dst = dalloc_n(&pl.desc, nt, s);
+    if (dst == BBTC_OK &&
+        (cudaMemcpyAsync(pl.desc, h_desc, sizeof(TaskDesc) * (size_t)nt, cudaMemcpyHostToDevice,
+                         s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess)) {
+      set_error("build_plan: copying the task descriptors failed");
+      dst = BBTC_ECUDA;
+    }
+    delete[] h_desc;
+    PLAN_TRY(dst);
+  }
 
   // work items: about 64 per resident warp in total, 64..4096 in-edges each
   // (or the caller's choice)
@@ -302,8 +468,8 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   PLAN_TRY(dalloc_n(&pl.scratch, SCR_TASKS + nt + g->ng, s));
   PLAN_TRY(configure_count_kernels(&pl));
 #undef PLAN_TRY
-  pl.bytes = (uint64_t)m * 12 + (uint64_t)nt * 24 + (uint64_t)pl.nitems * sizeof(WorkItem) +
-             (uint64_t)(SCR_TASKS + nt + g->ng) * 8;
+  pl.bytes = (uint64_t)m * 16 + (uint64_t)pl.total_rp * 4 + (uint64_t)nt * (24 + sizeof(TaskDesc)) +
+             (uint64_t)pl.nitems * sizeof(WorkItem) + (uint64_t)(SCR_TASKS + nt + g->ng) * 8;
   g->plan = pl;
   return BBTC_OK;
 }
