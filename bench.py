@@ -65,6 +65,44 @@ def make_graph(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def reduce_max_ms(ms: float, dist, device) -> float:
+    """Slowest rank's time: the job is done when every replica is."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job rate of `world` independent replicas, each doing units_per_rank."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
+def kernel_source_hash() -> str:
+    """sha256 of the counting kernel's source (a changed kernel voids old counters)."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_2009_12457_gb300", "csrc", "count.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def recorded_traffic(workload: str, p: int, kernel: str):
+    """DRAM bytes per counting-kernel launch from the committed ncu record, when it
+    was taken on this kernel source and this workload; else None."""
+    path = os.path.join(ROOT, "profiles", "k_count_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    for r in rec.get("records", []):
+        if (r.get("source_sha256") == kernel_source_hash() and r.get("workload") == workload
+                and r.get("p") == p and r.get("kernel") == kernel):
+            return r.get("dram_bytes_per_launch")
+    return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -328,6 +366,73 @@ def run_batch(args, world, rank, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ serving form
+
+def run_serve(args, world, rank, local_rank):
+    """Open-loop Poisson arrivals of count requests on R-MAT graphs of mixed scale
+    (10-22, edge factor 16; each request's graph seed is drawn from its id, from
+    a pool of `--serve-seeds` per scale so the device-resident cache can hit).
+    Reports p50/p99 latency and graphs/s at each arrival rate, against serial
+    plain per-request launches (create + count + destroy, no cache, no batching)."""
+    import torch
+    import graphgen
+    from paper_2009_12457_gb300 import serve
+
+    torch.cuda.set_device(local_rank)
+    scales = list(range(10, 23))
+    seeds = args.serve_seeds
+    rates = [float(x) for x in args.serve_rates.split(",")]
+
+    def key_of(rid):
+        d = graphgen.draw(5, 11, rid)
+        return (scales[d % len(scales)], (d >> 32) % seeds)
+
+    keys_all = [key_of(i) for i in range(200000)]
+    pool = {}
+    t0 = time.perf_counter()
+    for k in sorted(set(keys_all[:20000])):
+        pool[k] = graphgen.rmat(k[0], 16, 1000 * k[0] + k[1])
+    gen_s = time.perf_counter() - t0
+
+    def source(k):
+        if k not in pool:
+            pool[k] = graphgen.rmat(k[0], 16, 1000 * k[0] + k[1])
+        return pool[k]
+
+    # serial baseline on the first requests
+    nser = min(args.serve_serial, len(keys_all))
+    _, serial_gps = serve.serial_baseline(source, keys_all[:nser], symmetric=True, p=args.p)
+    results = []
+    offset = 0
+    for lam in rates:
+        arrivals = serve.poisson_trace(lam, args.serve_seconds, seed=5)
+        keys = keys_all[offset:offset + len(arrivals)]
+        offset += len(arrivals)
+        srv = serve.Server(source, device_budget_bytes=int(args.serve_budget_gb * (1 << 30)),
+                           max_batch=256, workers=2, p=args.p, symmetric=True)
+        try:
+            reqs = serve.run_open_loop(srv, keys, arrivals)
+        finally:
+            srv.close()
+        bad = [r for r in reqs if r.status != 0]
+        summ = serve.latency_summary(reqs)
+        summ.update({"rate_hz": lam, "failed": len(bad), "cache_hits": srv.hits,
+                     "cache_misses": srv.misses, "evictions": srv.evictions})
+        results.append(summ)
+    line = {
+        "metric": METRIC, "impl": "serve", "unit": "graphs/s",
+        "value": max(r["graphs_per_s"] for r in results), "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals, R-MAT scales 10-22, edge factor 16",
+                   "seconds_per_rate": args.serve_seconds, "seed_pool_per_scale": seeds,
+                   "device_cache_budget_gb": args.serve_budget_gb, "p": args.p,
+                   "host_generation_s": gen_s},
+        "serial_plain_graphs_per_s": serial_gps,
+        "rates": results,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------- GPU path
 
 def main():
@@ -341,6 +446,11 @@ def main():
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--kernel", default="auto", choices=["auto", "intersect", "hashmap"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-rates", default="200,500,1000,2000,5000")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seeds", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-serial", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
@@ -354,6 +464,9 @@ def main():
         return
     if args.workload.startswith("batch-"):
         run_batch(args, world, rank, local_rank)
+        return
+    if args.workload == "serve":
+        run_serve(args, world, rank, local_rank)
         return
 
     import torch
@@ -420,11 +533,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
     launches = bb.bbtc_kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max_ms(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
 
     # timed: host inputs through the same calls (H2D and count D2H inside)
     barrier()
@@ -437,11 +546,7 @@ def main():
         totals.add(total)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max_ms(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     barrier()
 
     if len(totals) != 1:
@@ -455,7 +560,7 @@ def main():
         h2d = (n + 1) * 8 + int(h_ci.numel()) * 4
         line = {
             "metric": METRIC,
-            "value": world * m / (ms / 1000.0),
+            "value": replica_throughput(m, world, ms),
             "unit": UNIT,
             "n_gpus": world,
             "steps": args.steps,
@@ -477,10 +582,11 @@ def main():
                 "phase_ms": {"prep": statistics.mean(prep_ms), "plan": statistics.mean(plan_ms),
                              "count_kernel": kms},
             },
-            "e2e": {"value": world * m / (e2e_ms / 1000.0), "unit": UNIT,
+            "e2e": {"value": replica_throughput(m, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": recorded_traffic(args.workload, p, args.kernel),
                          "kernel": "k_count (per-task counting, a9)",
                          "algorithmic_bytes": wmin,
                          "bytes_formula": "4*(m + sum over oriented edges (u,v) of d+(v))",

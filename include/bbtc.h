@@ -64,7 +64,10 @@ typedef struct {
   int32_t p;                    /* blocks per side, 1 <= p <= 64; 0 = choose from the graph */
   int32_t kernel;               /* bbtc_kernel */
   uint32_t timeout_ms;          /* 0 = no limit on the counting kernel's bounded waits */
-  uint64_t device_budget_bytes; /* 0 = graph resident; else blocks stream under this budget */
+  uint64_t device_budget_bytes; /* 0 = blocks resident; else the counting step keeps at most
+                                   this many bytes of blocks on the device, streaming them
+                                   from pinned host memory (the plan's block arrays move
+                                   there); preparation itself still uses device memory */
   uint64_t *per_vertex_out;     /* NULL, or n uint64 (ORIGINAL ids): triangles at each vertex */
   uint64_t *per_task_out;       /* NULL, or bbtc_num_tasks(p) uint64 in Alg. 4 order */
   void *stream;                 /* cudaStream_t to run on; NULL = the handle's own stream */
@@ -243,8 +246,12 @@ bbtc_status bbtc_graph_get_info(bbtc_graph_t g, bbtc_graph_info *info);
 typedef struct {
   double prep_ms;      /* bbtc_graph_create: a1-a4 (after any host-to-device copy) */
   double plan_ms;      /* last bbtc_count: a5-a8 (0 when the plan was reused) */
-  double count_ms;     /* last bbtc_count: the counting kernel (a9) */
+  double count_ms;     /* last bbtc_count: the counting kernel (a9); with a device
+                          budget, the whole streamed count (copies included) */
   int64_t work_items;  /* work items drained by that kernel */
+  int64_t stream_rounds;      /* last budgeted count: rounds of block copies */
+  uint64_t stream_h2d_bytes;  /* last budgeted count: block bytes copied to the device */
+  double stream_copy_ms;      /* last budgeted count: device time of those copies */
 } bbtc_timings;
 
 bbtc_status bbtc_graph_get_timings(bbtc_graph_t g, bbtc_timings *t);

@@ -79,6 +79,9 @@ class bbtc_timings(ctypes.Structure):
         ("plan_ms", ctypes.c_double),
         ("count_ms", ctypes.c_double),
         ("work_items", ctypes.c_int64),
+        ("stream_rounds", ctypes.c_int64),
+        ("stream_h2d_bytes", ctypes.c_uint64),
+        ("stream_copy_ms", ctypes.c_double),
     ]
 
 

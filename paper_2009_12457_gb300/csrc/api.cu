@@ -351,15 +351,10 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   DeviceGuard dg(g->device);
   const int p = opts.p == 0 ? default_p(g) : opts.p;
   cudaStream_t s = opts.stream ? (cudaStream_t)opts.stream : g->stream;
-  if (opts.device_budget_bytes != 0) {
-    const uint64_t need = g->bytes + (uint64_t)g->m * 12;
-    if (opts.device_budget_bytes < need) {
-      set_error("bbtc_count: a device budget of %llu bytes cannot hold the graph's blocks "
-                "(%llu bytes)", (unsigned long long)opts.device_budget_bytes,
-                (unsigned long long)need);
-      return BBTC_ENOMEM;
-    }
-  }
+  const bool budgeted = opts.device_budget_bytes != 0;
+  // a resident count needs the block arrays on the device: a plan that was
+  // streamed (its arrays now in host memory) is rebuilt
+  if (!budgeted && g->plan.streamed) free_plan(&g->plan, s);
   const bool rebuild = !plan_matches(g->plan, p, opts.kernel, opts.hash_threshold, opts.chunk);
   if (rebuild) BBTC_CUDA(cudaEventRecord(g->ev[2], s));
   BBTC_TRY(build_plan(g, p, opts.kernel, opts.hash_threshold, opts.chunk, s));
@@ -370,7 +365,18 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   unsigned long long *vertex_count = nullptr;
   if (opts.per_vertex_out) BBTC_TRY(scratch.get(&vertex_count, g->n));
   const bool per_graph = opts.per_graph_out != nullptr;
-  BBTC_TRY(run_count(g, pl, vertex_count, per_graph, opts.timeout_ms, s, g->ev[4], g->ev[5]));
+  if (budgeted) {
+    StreamStats st;
+    BBTC_TRY(run_count_streamed(g, g->plan, opts.device_budget_bytes, vertex_count, per_graph,
+                                opts.timeout_ms, s, &st));
+    g->stream_stats.rounds = st.rounds;
+    g->stream_stats.h2d_bytes = st.h2d_bytes;
+    g->stream_stats.copy_ms = st.copy_ms;
+    g->stream_stats_total_ms = st.total_ms;
+  } else {
+    BBTC_TRY(run_count(g, pl, vertex_count, per_graph, opts.timeout_ms, s, g->ev[4], g->ev[5]));
+    g->stream_stats_total_ms = -1.0;
+  }
   unsigned long long head[SCR_TASKS] = {0, 0, 0};
   BBTC_CUDA(cudaMemcpyAsync(head, pl.scratch, sizeof(head), cudaMemcpyDeviceToHost, s));
   BBTC_CUDA(cudaStreamSynchronize(s));
@@ -409,9 +415,10 @@ bbtc_status bbtc_count_async(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t 
   bbtc_opts opts;
   BBTC_TRY(check_opts(opts_in, &opts));
   const int p = opts.p == 0 ? default_p(g) : opts.p;
-  if (!plan_matches(g->plan, p, opts.kernel, opts.hash_threshold, opts.chunk)) {
-    set_error("bbtc_count_async: no plan for these options on the handle; build it with "
-              "bbtc_count or bbtc_graph_get_plan first");
+  if (!plan_matches(g->plan, p, opts.kernel, opts.hash_threshold, opts.chunk) ||
+      g->plan.streamed) {
+    set_error("bbtc_count_async: no resident plan for these options on the handle; build it "
+              "with bbtc_count (without a device budget) or bbtc_graph_get_plan first");
     return BBTC_EINVAL;
   }
   if (opts.per_vertex_out ||
@@ -539,8 +546,12 @@ bbtc_status bbtc_graph_get_timings(bbtc_graph_t g, bbtc_timings *t) {
   };
   t->prep_ms = elapsed(g->ev[0], g->ev[1]);
   t->plan_ms = g->plan_timed ? elapsed(g->ev[2], g->ev[3]) : 0.0;
-  t->count_ms = elapsed(g->ev[4], g->ev[5]);
+  t->count_ms = g->stream_stats_total_ms >= 0 ? g->stream_stats_total_ms
+                                              : elapsed(g->ev[4], g->ev[5]);
   t->work_items = g->plan.nitems;
+  t->stream_rounds = g->stream_stats.rounds;
+  t->stream_h2d_bytes = g->stream_stats.h2d_bytes;
+  t->stream_copy_ms = g->stream_stats.copy_ms;
   return BBTC_OK;
 }
 

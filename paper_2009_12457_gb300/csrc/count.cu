@@ -119,13 +119,17 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
     const int t = w.task;
     const bool use_hash = (w.flags & 1) != 0;
     const TaskDesc &d = P.desc[t];
-    const int32_t *__restrict__ ie_u = d.ie_u - d.ie_off;
-    const int32_t *__restrict__ ie_v = d.ie_v - d.ie_off;
-    const uint32_t *__restrict__ ie_e = d.ie_e - d.ie_off;
+    // block arrays are indexed locally: in-edge x at [x - ie_off], column
+    // position q at [q - ci_*_off] (the offsets are 0 when the plan is resident)
+    const int32_t *__restrict__ ie_u = d.ie_u;
+    const int32_t *__restrict__ ie_v = d.ie_v;
+    const uint32_t *__restrict__ ie_e = d.ie_e;
+    const int64_t ie_off = d.ie_off;
     const uint32_t *__restrict__ rp_ik = d.rp_ik;
     const uint32_t *__restrict__ rp_jk = d.rp_jk;
-    const int32_t *__restrict__ ci_ik = d.ci_ik - d.ci_ik_off;  // indexed by position
-    const int32_t *__restrict__ ci_jk = d.ci_jk - d.ci_jk_off;
+    const int32_t *__restrict__ ci_ik = d.ci_ik;
+    const int32_t *__restrict__ ci_jk = d.ci_jk;
+    const int64_t ik_off = d.ci_ik_off, jk_off = d.ci_jk_off;
     const int32_t c_i = d.c_i, c_j = d.c_j;
     const bool diag = d.diag != 0;
     unsigned long long acc = 0;
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
     while (base < w.x1) {
       const int64_t x = base + lane;
       const bool valid = x < w.x1;
-      const int32_t v = valid ? ie_v[x] : -1;
+      const int32_t v = valid ? ie_v[x - ie_off] : -1;
       // in-edges are sorted by destination: lanes equal to lane 0's v form a prefix
       const int32_t v0 = __shfl_sync(0xffffffffu, v, 0);
       const unsigned eq = __ballot_sync(0xffffffffu, valid && v == v0);
@@ -158,28 +162,28 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
       int32_t u = 0;
       int64_t e = 0;
       if (active) {
-        u = ie_u[x];
-        e = ie_e[x];
+        u = ie_u[x - ie_off];
+        e = ie_e[x - ie_off];
       }
-      // N(G_jk, v): direct row pointers of block (j, k)
+      // N(G_jk, v): direct row pointers of block (j, k); [b0, b1) local to ci_jk
       int64_t b0 = 0, b1 = 0;
       if (uniform) {
         if (lane == 0) {
-          b0 = rp_jk[v0 - c_j];
-          b1 = rp_jk[v0 - c_j + 1];
+          b0 = (int64_t)rp_jk[v0 - c_j] - jk_off;
+          b1 = (int64_t)rp_jk[v0 - c_j + 1] - jk_off;
         }
         b0 = __shfl_sync(0xffffffffu, b0, 0);
         b1 = __shfl_sync(0xffffffffu, b1, 0);
       } else if (active) {
-        b0 = rp_jk[v - c_j];
-        b1 = rp_jk[v - c_j + 1];
+        b0 = (int64_t)rp_jk[v - c_j] - jk_off;
+        b1 = (int64_t)rp_jk[v - c_j + 1] - jk_off;
       }
       // N(G_ik, u) restricted to entries above v (for k == j, the entries of
-      // G_ij after (u, v) itself)
+      // G_ij after (u, v) itself); [s0, s1) local to ci_ik
       int64_t s0 = 0, s1 = 0;
       if (active && b1 > b0) {
-        s1 = rp_ik[u - c_i + 1];
-        s0 = diag ? e + 1 : rp_ik[u - c_i];
+        s1 = (int64_t)rp_ik[u - c_i + 1] - ik_off;
+        s0 = diag ? e + 1 - ik_off : (int64_t)rp_ik[u - c_i] - ik_off;
       }
       const uint32_t len = (uint32_t)(s1 - s0);
       const uint32_t incl = warp_inclusive_scan(len);
@@ -372,47 +376,64 @@ bbtc_status wedge_sums(const bbtc_graph *g, uint64_t *in_sum, uint64_t *out_sum,
   return BBTC_OK;
 }
 
-bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
-                      bool per_graph, uint32_t timeout_ms, cudaStream_t s,
-                      cudaEvent_t ev_begin, cudaEvent_t ev_end) {
-  const int64_t nt = pl.ntasks;
+bbtc_status count_reset(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
+                        bool per_graph, cudaStream_t s) {
   const int ng = per_graph ? g->ng : 0;
-  unsigned long long *scr = pl.scratch;
-  BBTC_CUDA(cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (size_t)(SCR_TASKS + nt + ng),
-                            s));
+  BBTC_CUDA(cudaMemsetAsync(pl.scratch, 0,
+                            sizeof(unsigned long long) * (size_t)(SCR_TASKS + pl.ntasks + ng), s));
   if (vertex_count)
     BBTC_CUDA(cudaMemsetAsync(vertex_count, 0,
                               sizeof(unsigned long long) * (size_t)(g->n > 0 ? g->n : 1), s));
-  if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
-  if (pl.nitems > 0) {
-    CountParams P;
-    P.desc = pl.desc;
-    P.items = pl.items;
-    P.nitems = pl.nitems;
-    P.head = scr + SCR_HEAD;
-    P.task_count = scr + SCR_TASKS;
-    P.vcount = vertex_count;
-    P.gid = g->gid;
-    P.graph_count = scr + SCR_TASKS + nt;
-    P.status = reinterpret_cast<int32_t *>(scr + SCR_STATUS);
-    P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
-    const int mode = (vertex_count ? MODE_VERTEX : 0) | (per_graph ? MODE_GRAPH : 0);
-    int64_t blocks = (int64_t)num_sms() * pl.blocks_per_sm[mode];
-    const int64_t need = (pl.nitems + CT_NT / 32 - 1) / (CT_NT / 32);
-    if (blocks > need) blocks = need;
-    const size_t smem = count_smem_bytes();
-    switch (mode) {
-      case 0: k_count<0><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
-      case 1: k_count<1><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
-      case 2: k_count<2><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
-      default: k_count<3><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
-    }
-    BBTC_LAUNCH_CHECK();
+  return BBTC_OK;
+}
+
+bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t nitems,
+                         unsigned long long *vertex_count, bool per_graph, uint32_t timeout_ms,
+                         cudaStream_t s) {
+  if (nitems <= 0) return BBTC_OK;
+  unsigned long long *scr = pl.scratch;
+  BBTC_CUDA(cudaMemsetAsync(scr + SCR_HEAD, 0, sizeof(unsigned long long), s));
+  CountParams P;
+  P.desc = pl.desc;
+  P.items = pl.items + item0;
+  P.nitems = nitems;
+  P.head = scr + SCR_HEAD;
+  P.task_count = scr + SCR_TASKS;
+  P.vcount = vertex_count;
+  P.gid = g->gid;
+  P.graph_count = scr + SCR_TASKS + pl.ntasks;
+  P.status = reinterpret_cast<int32_t *>(scr + SCR_STATUS);
+  P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
+  const int mode = (vertex_count ? MODE_VERTEX : 0) | (per_graph ? MODE_GRAPH : 0);
+  int64_t blocks = (int64_t)num_sms() * pl.blocks_per_sm[mode];
+  const int64_t need = (nitems + CT_NT / 32 - 1) / (CT_NT / 32);
+  if (blocks > need) blocks = need;
+  const size_t smem = count_smem_bytes();
+  switch (mode) {
+    case 0: k_count<0><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+    case 1: k_count<1><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+    case 2: k_count<2><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+    default: k_count<3><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
   }
-  if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
-  k_sum_u64<<<grid_for(nt, 256, 2), 256, 0, s>>>(scr + SCR_TASKS, nt, scr + SCR_TOTAL);
   BBTC_LAUNCH_CHECK();
   return BBTC_OK;
+}
+
+bbtc_status count_finish(const Plan &pl, cudaStream_t s) {
+  k_sum_u64<<<grid_for(pl.ntasks, 256, 2), 256, 0, s>>>(pl.scratch + SCR_TASKS, pl.ntasks,
+                                                         pl.scratch + SCR_TOTAL);
+  BBTC_LAUNCH_CHECK();
+  return BBTC_OK;
+}
+
+bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
+                      bool per_graph, uint32_t timeout_ms, cudaStream_t s,
+                      cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+  BBTC_TRY(count_reset(g, pl, vertex_count, per_graph, s));
+  if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
+  BBTC_TRY(count_launch(g, pl, 0, pl.nitems, vertex_count, per_graph, timeout_ms, s));
+  if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
+  return count_finish(pl, s);
 }
 
 }  // namespace bbtc
@@ -473,7 +494,7 @@ extern "C" bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *c
     return BBTC_EINVAL;
   }
   const Plan &pl = g->plan;
-  if (pl.p != p) {
+  if (pl.p != p || pl.streamed) {
     set_error("bbtc_count_noalloc: no plan for p = %d on this handle; call bbtc_count or "
               "bbtc_graph_get_plan with that p first", p);
     return BBTC_EINVAL;

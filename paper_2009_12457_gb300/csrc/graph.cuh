@@ -69,12 +69,25 @@ struct Plan {
   // [2] total, [3, 3+T) per-task counts, [3+T, 3+T+ng) per-graph counts
   unsigned long long *scratch = nullptr;
   int blocks_per_sm[4] = {0, 0, 0, 0};  // occupancy of each counting-kernel mode
+  // streamed mode: the block arrays live in pinned host memory instead
+  bool streamed = false;
+  uint32_t *h_rp = nullptr;
+  int32_t *h_ci = nullptr;
+  int32_t *h_ie_u = nullptr;
+  int32_t *h_ie_v = nullptr;
+  uint32_t *h_ie_e = nullptr;
   uint64_t bytes = 0;
 };
 
 constexpr int SCR_HEAD = 0, SCR_STATUS = 1, SCR_TOTAL = 2, SCR_TASKS = 3;
 
 }  // namespace bbtc
+
+struct StreamStatsLite {
+  int64_t rounds = 0;
+  uint64_t h2d_bytes = 0;
+  double copy_ms = 0;
+};
 
 struct bbtc_graph {
   int64_t n = 0;
@@ -97,6 +110,8 @@ struct bbtc_graph {
   bbtc::Plan plan;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool plan_timed = false;
+  StreamStatsLite stream_stats;
+  double stream_stats_total_ms = -1.0;  // >= 0 when the last count was streamed
   bool wedges_known = false;
   uint64_t wedges_in = 0, wedges_out = 0;
 };
@@ -117,6 +132,7 @@ inline bool plan_matches(const Plan &pl, int p, int kernel_mode, int hash_thresh
          pl.chunk_req == chunk;
 }
 void free_plan(Plan *pl, cudaStream_t s);
+void free_plan_host(Plan *pl);  // pinned host copies of a streamed plan
 
 // Occupancy of the counting kernel (set at plan time so that a count only
 // enqueues work).
@@ -128,6 +144,25 @@ bbtc_status configure_count_kernels(Plan *pl);
 bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                       bool per_graph, uint32_t timeout_ms, cudaStream_t s,
                       cudaEvent_t ev_begin, cudaEvent_t ev_end);
+// The three parts of run_count: zero the outputs, drain items [item0,
+// item0 + nitems) in one persistent launch (accumulating), sum the tasks.
+bbtc_status count_reset(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
+                        bool per_graph, cudaStream_t s);
+bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t nitems,
+                         unsigned long long *vertex_count, bool per_graph, uint32_t timeout_ms,
+                         cudaStream_t s);
+bbtc_status count_finish(const Plan &pl, cudaStream_t s);
+
+// a11: count with the blocks streamed from pinned host memory through a
+// device pool of `budget` bytes (two halves, double-buffered).
+struct StreamStats {
+  int64_t rounds = 0;
+  uint64_t h2d_bytes = 0;
+  double copy_ms = 0, count_ms = 0, total_ms = 0;
+};
+bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
+                               unsigned long long *vertex_count, bool per_graph,
+                               uint32_t timeout_ms, cudaStream_t s, StreamStats *stats);
 
 // Work figures of the oriented graph (device): sum_{(u,v)} d+(v) and
 // sum_u d+(u)(d+(u)-1)/2.

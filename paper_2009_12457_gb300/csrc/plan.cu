@@ -70,66 +70,69 @@ __global__ void k_inedge_finish(const uint64_t *__restrict__ keys,
   }
 }
 
-// BCSR, step 1: for every (block (a,b), row x of V_a) the number of entries of
-// row c_a + x in V_b and where they start in the oriented CSR. The trailing
-// slot of each block's segment counts 0 (it becomes the block's end).
-__global__ void k_bcsr_count(const int64_t *__restrict__ rowptr,
-                             const int32_t *__restrict__ colidx,
-                             const int32_t *__restrict__ cuts_g, int p, int nblk,
-                             const int64_t *__restrict__ seg_g, const int32_t *__restrict__ blk_g,
-                             int64_t total, uint64_t *__restrict__ cnt,
+// BCSR, step 1 (one thread per oriented edge e = (u, v)): the edge falls in
+// block (part(u), part(v)) at row slot rpb[part(u)*p + part(v)] + (u - c_a).
+// Count the edges of every slot (warp-aggregated: consecutive edges share
+// slots) and record where each slot's run starts in the oriented CSR (rows
+// are sorted, so a slot's edges are consecutive).
+__global__ void k_bcsr_count(const int32_t *__restrict__ esrc,
+                             const int32_t *__restrict__ colidx, int64_t m,
+                             const int32_t *__restrict__ cuts_g, int p,
+                             const int64_t *__restrict__ rpb_g,
+                             unsigned long long *__restrict__ cnt,
                              uint32_t *__restrict__ start) {
   __shared__ int32_t cuts[MAXP + 1];
-  __shared__ int64_t seg[MAXP * (MAXP + 1) / 2 + 1];
-  __shared__ int32_t blk[MAXP * (MAXP + 1) / 2];
+  __shared__ int64_t rpb[MAXP * MAXP];
   for (int i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
-  for (int i = threadIdx.x; i <= nblk; i += blockDim.x) seg[i] = seg_g[i];
-  for (int i = threadIdx.x; i < nblk; i += blockDim.x) blk[i] = blk_g[i];
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) rpb[i] = rpb_g[i];
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = nblk;  // last block whose segment starts at or before i
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (seg[mid] <= i) lo = mid; else hi = mid;
+  const unsigned lane = threadIdx.x & 31u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < m; base += stride) {
+    const int64_t e = base + threadIdx.x;
+    int64_t slot = -1;
+    if (e < m) {
+      const int32_t u = esrc[e], v = colidx[e];
+      const int a = part_of_dev(cuts, p, u), b = part_of_dev(cuts, p, v);
+      slot = rpb[a * p + b] + (u - cuts[a]);
+      const bool run_head = e == 0 || esrc[e - 1] != u || part_of_dev(cuts, p, colidx[e - 1]) != b;
+      if (run_head) start[slot] = (uint32_t)e;
     }
-    const int a = blk[lo] >> 8, b = blk[lo] & 0xff;
-    const int64_t x = i - seg[lo];
-    uint64_t c = 0;
-    uint32_t st = 0;
-    if (x < (int64_t)(cuts[a + 1] - cuts[a])) {
-      const int64_t u = cuts[a] + x;
-      const int64_t rs = rowptr[u], re = rowptr[u + 1];
-      // entries of row u are above u >= c_a, so those in V_a start the row
-      const int64_t S = b == a ? rs : lower_bound_dev<int32_t, int64_t>(colidx, rs, re, cuts[b]);
-      const int64_t E = b == p - 1 ? re : lower_bound_dev<int32_t, int64_t>(colidx, S, re, cuts[b + 1]);
-      c = (uint64_t)(E - S);
-      st = (uint32_t)S;
-    }
-    cnt[i] = c;
-    start[i] = st;
+    const unsigned peers = __match_any_sync(0xffffffffu, slot);
+    if (slot >= 0 && lane == (unsigned)(__ffs(peers) - 1))
+      atomicAdd(&cnt[slot], (unsigned long long)__popc(peers));
   }
 }
 
-// BCSR, step 2: copy each (row, block) run of columns to its block-major
-// position, record where every CSR edge went, and narrow the positions.
-__global__ void k_bcsr_fill(const int32_t *__restrict__ colidx, const uint64_t *__restrict__ pos,
-                            const uint32_t *__restrict__ start, int64_t total,
-                            int32_t *__restrict__ ci, uint32_t *__restrict__ pos_of_edge,
-                            uint32_t *__restrict__ rp) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t q0 = pos[i];
-    rp[i] = (uint32_t)q0;
-    if (i + 1 < total) {
-      const uint64_t len = pos[i + 1] - q0;
-      const uint32_t S = start[i];
-      for (uint64_t t = 0; t < len; ++t) {
-        ci[q0 + t] = colidx[S + t];
-        pos_of_edge[S + t] = (uint32_t)(q0 + t);
-      }
-    }
+// BCSR, step 2 (one thread per oriented edge): copy the column to its
+// block-major position and record the position for the in-edges.
+__global__ void k_bcsr_fill(const int32_t *__restrict__ esrc, const int32_t *__restrict__ colidx,
+                            int64_t m, const int32_t *__restrict__ cuts_g, int p,
+                            const int64_t *__restrict__ rpb_g, const uint64_t *__restrict__ pos,
+                            const uint32_t *__restrict__ start, int32_t *__restrict__ ci,
+                            uint32_t *__restrict__ pos_of_edge) {
+  __shared__ int32_t cuts[MAXP + 1];
+  __shared__ int64_t rpb[MAXP * MAXP];
+  for (int i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) rpb[i] = rpb_g[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = esrc[e], v = colidx[e];
+    const int a = part_of_dev(cuts, p, u), b = part_of_dev(cuts, p, v);
+    const int64_t slot = rpb[a * p + b] + (u - cuts[a]);
+    const uint64_t dest = pos[slot] + (uint64_t)(e - (int64_t)start[slot]);
+    ci[dest] = v;
+    pos_of_edge[e] = (uint32_t)dest;
   }
+}
+
+// BCSR, step 3: the row pointers are the scanned slot counts, narrowed.
+__global__ void k_bcsr_rowptr(const uint64_t *__restrict__ pos, int64_t total,
+                              uint32_t *__restrict__ rp) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x)
+    rp[i] = (uint32_t)pos[i];
 }
 
 // boff[i*(p+1)+j] = first in-edge of part i whose destination is >= c_j.
@@ -253,6 +256,7 @@ void free_plan(Plan *pl, cudaStream_t s) {
   dfree(pl->rp, s);
   dfree(pl->ci, s);
   dfree(pl->desc, s);
+  free_plan_host(pl);
   *pl = Plan();
 }
 
@@ -303,49 +307,44 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
     free_plan(&pl, s);
     return BBTC_ECUDA;
   }
-  const int nblk = p * (p + 1) / 2;
-  int64_t h_seg[MAXP * (MAXP + 1) / 2 + 1];
-  int32_t h_blk[MAXP * (MAXP + 1) / 2];
   {
-    int bi = 0;
     int64_t off = 0;
     for (int a = 0; a < p; ++a)
       for (int b = a; b < p; ++b) {
-        h_seg[bi] = off;
-        h_blk[bi] = (a << 8) | b;
         pl.h_rpb[a * p + b] = off;
         off += (int64_t)(pl.h_cuts[a + 1] - pl.h_cuts[a]) + 1;
-        ++bi;
       }
-    h_seg[nblk] = off;
     pl.total_rp = off;
   }
-  int64_t *d_seg = nullptr;
-  int32_t *d_blk = nullptr;
+  int64_t *d_rpb = nullptr;
   uint64_t *cnt = nullptr;
   uint32_t *start = nullptr, *pos_of_edge = nullptr;
-  PLAN_TRY(scratch.get(&d_seg, nblk + 1));
-  PLAN_TRY(scratch.get(&d_blk, nblk));
+  PLAN_TRY(scratch.get(&d_rpb, (int64_t)p * p));
   PLAN_TRY(scratch.get(&cnt, pl.total_rp));
   PLAN_TRY(scratch.get(&start, pl.total_rp));
   PLAN_TRY(scratch.get(&pos_of_edge, m));
   PLAN_TRY(dalloc_n(&pl.rp, pl.total_rp, s));
   PLAN_TRY(dalloc_n(&pl.ci, m, s));
-  if (cudaMemcpyAsync(d_seg, h_seg, sizeof(int64_t) * (size_t)(nblk + 1), cudaMemcpyHostToDevice,
+  if (cudaMemcpyAsync(d_rpb, pl.h_rpb, sizeof(int64_t) * (size_t)p * p, cudaMemcpyHostToDevice,
                       s) != cudaSuccess ||
-      cudaMemcpyAsync(d_blk, h_blk, sizeof(int32_t) * (size_t)nblk, cudaMemcpyHostToDevice, s) !=
-          cudaSuccess) {
+      cudaMemsetAsync(cnt, 0, sizeof(uint64_t) * (size_t)pl.total_rp, s) != cudaSuccess) {
     set_error("build_plan: copying the block table failed");
     free_plan(&pl, s);
     return BBTC_ECUDA;
   }
-  k_bcsr_count<<<grid_for(pl.total_rp, 256, 32), 256, 0, s>>>(
-      g->rowptr, g->colidx, pl.cuts, p, nblk, d_seg, d_blk, pl.total_rp, cnt, start);
-  PLAN_TRY(launch_status("build_plan"));
+  if (m > 0) {
+    k_bcsr_count<<<grid_for(m, 256, 32), 256, 0, s>>>(
+        g->esrc, g->colidx, m, pl.cuts, p, d_rpb,
+        reinterpret_cast<unsigned long long *>(cnt), start);
+    PLAN_TRY(launch_status("build_plan"));
+  }
   PLAN_TRY(exclusive_scan_u64(cnt, cnt, pl.total_rp, s));
-  k_bcsr_fill<<<grid_for(pl.total_rp, 256, 32), 256, 0, s>>>(g->colidx, cnt, start,
-                                                              pl.total_rp, pl.ci, pos_of_edge,
-                                                              pl.rp);
+  if (m > 0) {
+    k_bcsr_fill<<<grid_for(m, 256, 32), 256, 0, s>>>(g->esrc, g->colidx, m, pl.cuts, p, d_rpb,
+                                                     cnt, start, pl.ci, pos_of_edge);
+    PLAN_TRY(launch_status("build_plan"));
+  }
+  k_bcsr_rowptr<<<grid_for(pl.total_rp, 256, 32), 256, 0, s>>>(cnt, pl.total_rp, pl.rp);
   PLAN_TRY(launch_status("build_plan"));
 
   // in-edges grouped by (part(u), v, u), and the block offsets

@@ -1,0 +1,317 @@
+// stream.cu -- a11: counting with the blocks streamed from pinned host memory.
+//
+// When a caller gives bbtc_count a device budget, the plan's block arrays
+// (each block G_ab's row pointers and columns, and each block's in-edges) move
+// to pinned host memory. Tasks are then processed in the plan's order, in
+// rounds: a round is the longest run of consecutive tasks whose distinct
+// blocks fit in half of a device pool of `budget` bytes. While the tasks of
+// one round are counted on the compute stream, the blocks of the next round are
+// copied into the other half on a copy stream (the paper's prefetch of the next
+// task's blocks, Alg. 7), and each task's descriptor is rewritten to point at
+// its blocks' copies. Counts accumulate across rounds exactly as in one launch.
+#include <stdio.h>
+
+#include <map>
+#include <new>
+#include <vector>
+
+#include "graph.cuh"
+
+namespace bbtc {
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+template <typename T>
+bbtc_status to_pinned(T **host, T **dev, int64_t count, cudaStream_t s) {
+  const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+  BBTC_CUDA(cudaHostAlloc(reinterpret_cast<void **>(host), bytes, cudaHostAllocDefault));
+  if (count > 0) BBTC_CUDA(cudaMemcpyAsync(*host, *dev, sizeof(T) * (size_t)count,
+                                           cudaMemcpyDeviceToHost, s));
+  return BBTC_OK;
+}
+
+// Moves the block arrays of a resident plan to pinned host memory.
+bbtc_status plan_to_host(Plan &pl, int64_t m, cudaStream_t s) {
+  if (pl.streamed) return BBTC_OK;
+  BBTC_TRY(to_pinned(&pl.h_rp, &pl.rp, pl.total_rp, s));
+  BBTC_TRY(to_pinned(&pl.h_ci, &pl.ci, m, s));
+  BBTC_TRY(to_pinned(&pl.h_ie_u, &pl.ie_u, m, s));
+  BBTC_TRY(to_pinned(&pl.h_ie_v, &pl.ie_v, m, s));
+  BBTC_TRY(to_pinned(&pl.h_ie_e, &pl.ie_e, m, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  dfree(pl.rp, s);
+  dfree(pl.ci, s);
+  dfree(pl.ie_u, s);
+  dfree(pl.ie_v, s);
+  dfree(pl.ie_e, s);
+  pl.rp = nullptr;
+  pl.ci = nullptr;
+  pl.ie_u = pl.ie_v = nullptr;
+  pl.ie_e = nullptr;
+  pl.streamed = true;
+  return BBTC_OK;
+}
+
+// A block in the pool: kind 0 = BCSR block (a, b) (row pointers, then
+// columns), kind 1 = in-edges of block (a, b) (u, v, position).
+struct BlockKey {
+  int kind, a, b;
+  bool operator<(const BlockKey &o) const {
+    return kind != o.kind ? kind < o.kind : (a != o.a ? a < o.a : b < o.b);
+  }
+};
+
+struct Run {  // the work items of one task, in plan order
+  int32_t task;
+  int64_t item0, item1;
+};
+
+}  // namespace
+
+void free_plan_host(Plan *pl) {
+  if (pl->h_rp) cudaFreeHost(pl->h_rp);
+  if (pl->h_ci) cudaFreeHost(pl->h_ci);
+  if (pl->h_ie_u) cudaFreeHost(pl->h_ie_u);
+  if (pl->h_ie_v) cudaFreeHost(pl->h_ie_v);
+  if (pl->h_ie_e) cudaFreeHost(pl->h_ie_e);
+  pl->h_rp = nullptr;
+  pl->h_ci = nullptr;
+  pl->h_ie_u = pl->h_ie_v = nullptr;
+  pl->h_ie_e = nullptr;
+}
+
+bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
+                               unsigned long long *vertex_count, bool per_graph,
+                               uint32_t timeout_ms, cudaStream_t s, StreamStats *stats) {
+  const int p = pl.p;
+  const int64_t nt = pl.ntasks;
+  BBTC_TRY(plan_to_host(pl, g->m, s));
+
+  // small plan tables on the host
+  std::vector<WorkItem> items((size_t)pl.nitems);
+  std::vector<int64_t> boff((size_t)p * (p + 1));
+  if (pl.nitems > 0)
+    BBTC_CUDA(cudaMemcpyAsync(items.data(), pl.items, sizeof(WorkItem) * (size_t)pl.nitems,
+                              cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaMemcpyAsync(boff.data(), pl.boff, sizeof(int64_t) * boff.size(),
+                            cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> ti((size_t)nt), tj((size_t)nt), tk((size_t)nt);
+  {
+    int64_t t = 0;
+    for (int i = 0; i < p; ++i)
+      for (int j = i; j < p; ++j)
+        for (int k = j; k < p; ++k, ++t) {
+          ti[(size_t)t] = i;
+          tj[(size_t)t] = j;
+          tk[(size_t)t] = k;
+        }
+  }
+  std::vector<Run> runs;
+  for (int64_t x = 0; x < pl.nitems; ++x) {
+    if (runs.empty() || runs.back().task != items[(size_t)x].task)
+      runs.push_back(Run{items[(size_t)x].task, x, x});
+    runs.back().item1 = x + 1;
+  }
+
+  auto vsize = [&](int a) -> int64_t { return (int64_t)(pl.h_cuts[a + 1] - pl.h_cuts[a]); };
+  auto col0 = [&](int a, int b) -> int64_t { return (int64_t)pl.h_rp[pl.h_rpb[a * p + b]]; };
+  auto col1 = [&](int a, int b) -> int64_t {
+    return (int64_t)pl.h_rp[pl.h_rpb[a * p + b] + vsize(a)];
+  };
+  auto ie0 = [&](int a, int b) -> int64_t { return boff[(size_t)(a * (p + 1) + b)]; };
+  auto ie1 = [&](int a, int b) -> int64_t { return boff[(size_t)(a * (p + 1) + b + 1)]; };
+  auto block_bytes = [&](const BlockKey &k) -> size_t {
+    if (k.kind == 0)
+      return align_up(4 * (size_t)(vsize(k.a) + 1)) + align_up(4 * (size_t)(col1(k.a, k.b) - col0(k.a, k.b)));
+    return 3 * align_up(4 * (size_t)(ie1(k.a, k.b) - ie0(k.a, k.b)));
+  };
+
+  const size_t half = (size_t)(budget / 2) & ~(ALIGN - 1);
+  Scratch scratch(s);
+  unsigned char *pool = nullptr;
+  BBTC_TRY(scratch.get(&pool, (int64_t)(2 * half)));
+  cudaStream_t cs = nullptr;
+  cudaEvent_t copy_done[2] = {nullptr, nullptr}, kern_done[2] = {nullptr, nullptr};
+  cudaEvent_t t_begin = nullptr, t_end = nullptr;
+  TaskDesc *stage[2] = {nullptr, nullptr};  // pinned staging of descriptors per half
+  bbtc_status st = BBTC_OK;
+  bool used_half[2] = {false, false};
+  int64_t round = 0;
+  float copy_ms_total = 0.f;
+  do {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&copy_done[0]) != cudaSuccess ||
+        cudaEventCreate(&copy_done[1]) != cudaSuccess ||
+        cudaEventCreate(&kern_done[0]) != cudaSuccess ||
+        cudaEventCreate(&kern_done[1]) != cudaSuccess || cudaEventCreate(&t_begin) != cudaSuccess ||
+        cudaEventCreate(&t_end) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void **>(&stage[0]), sizeof(TaskDesc) * (size_t)(nt > 0 ? nt : 1),
+                      cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void **>(&stage[1]), sizeof(TaskDesc) * (size_t)(nt > 0 ? nt : 1),
+                      cudaHostAllocDefault) != cudaSuccess) {
+      set_error("streamed count: creating streams, events or staging buffers failed");
+      st = BBTC_ECUDA;
+      break;
+    }
+    if ((st = count_reset(g, pl, vertex_count, per_graph, s)) != BBTC_OK) break;
+    if (cudaEventRecord(t_begin, s) != cudaSuccess) { st = BBTC_ECUDA; break; }
+    size_t pos = 0;
+    while (pos < runs.size() && st == BBTC_OK) {
+      // the longest run of tasks whose distinct blocks fit in one half
+      std::map<BlockKey, size_t> placed;
+      size_t used = 0, first = pos;
+      while (pos < runs.size()) {
+        const int t = runs[pos].task;
+        const BlockKey need[3] = {{1, ti[t], tj[t]}, {0, ti[t], tk[t]}, {0, tj[t], tk[t]}};
+        size_t add = 0;
+        bool fresh[3] = {false, false, false};
+        for (int q = 0; q < 3; ++q) {
+          bool dup = placed.count(need[q]) > 0;
+          for (int r = 0; r < q; ++r) dup = dup || (fresh[r] && !(need[r] < need[q]) && !(need[q] < need[r]));
+          if (!dup) {
+            fresh[q] = true;
+            add += block_bytes(need[q]);
+          }
+        }
+        if (used + add > half) break;
+        for (int q = 0; q < 3; ++q)
+          if (fresh[q]) {
+            placed[need[q]] = used;
+            used += block_bytes(need[q]);
+          }
+        ++pos;
+      }
+      if (pos == first) {
+        const int t = runs[pos].task;
+        set_error("streamed count: the blocks of task (%d,%d,%d) do not fit in half of a %llu-byte "
+                  "device budget", ti[t], tj[t], tk[t], (unsigned long long)budget);
+        st = BBTC_ENOMEM;
+        break;
+      }
+      const int h = (int)(round & 1);
+      unsigned char *base = pool + (size_t)h * half;
+      // the previous round in this half must have finished before its blocks
+      // and descriptor staging are overwritten
+      if (used_half[h]) {
+        if (cudaStreamWaitEvent(cs, kern_done[h], 0) != cudaSuccess ||
+            cudaEventSynchronize(copy_done[h]) != cudaSuccess) {
+          st = BBTC_ECUDA;
+          break;
+        }
+      }
+      cudaEvent_t c0 = nullptr, c1 = nullptr;
+      cudaEventCreate(&c0);
+      cudaEventCreate(&c1);
+      cudaEventRecord(c0, cs);
+      for (const auto &kv : placed) {
+        const BlockKey &k = kv.first;
+        unsigned char *dst = base + kv.second;
+        cudaError_t e1 = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess;
+        if (k.kind == 0) {
+          const int64_t nrp = vsize(k.a) + 1, c0i = col0(k.a, k.b), nci = col1(k.a, k.b) - c0i;
+          e1 = cudaMemcpyAsync(dst, pl.h_rp + pl.h_rpb[k.a * p + k.b], 4 * (size_t)nrp,
+                               cudaMemcpyHostToDevice, cs);
+          if (nci > 0)
+            e2 = cudaMemcpyAsync(dst + align_up(4 * (size_t)nrp), pl.h_ci + c0i, 4 * (size_t)nci,
+                                 cudaMemcpyHostToDevice, cs);
+          stats->h2d_bytes += 4 * (uint64_t)(nrp + nci);
+        } else {
+          const int64_t x0 = ie0(k.a, k.b), len = ie1(k.a, k.b) - x0;
+          const size_t seg = align_up(4 * (size_t)len);
+          if (len > 0) {
+            e1 = cudaMemcpyAsync(dst, pl.h_ie_u + x0, 4 * (size_t)len, cudaMemcpyHostToDevice, cs);
+            e2 = cudaMemcpyAsync(dst + seg, pl.h_ie_v + x0, 4 * (size_t)len, cudaMemcpyHostToDevice, cs);
+            e3 = cudaMemcpyAsync(dst + 2 * seg, pl.h_ie_e + x0, 4 * (size_t)len,
+                                 cudaMemcpyHostToDevice, cs);
+          }
+          stats->h2d_bytes += 12 * (uint64_t)len;
+        }
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+          set_error("streamed count: host-to-device block copy failed");
+          st = BBTC_ECUDA;
+          break;
+        }
+      }
+      if (st != BBTC_OK) break;
+      // descriptors of the round's tasks, pointing into this half
+      for (size_t r = first; r < pos; ++r) {
+        const int t = runs[r].task;
+        const int i = ti[t], j = tj[t], k = tk[t];
+        const size_t o_ie = placed[BlockKey{1, i, j}];
+        const size_t o_ik = placed[BlockKey{0, i, k}];
+        const size_t o_jk = placed[BlockKey{0, j, k}];
+        const size_t seg = align_up(4 * (size_t)(ie1(i, j) - ie0(i, j)));
+        TaskDesc &d = stage[h][t];
+        d.ie_u = reinterpret_cast<const int32_t *>(base + o_ie);
+        d.ie_v = reinterpret_cast<const int32_t *>(base + o_ie + seg);
+        d.ie_e = reinterpret_cast<const uint32_t *>(base + o_ie + 2 * seg);
+        d.ie_off = ie0(i, j);
+        d.rp_ik = reinterpret_cast<const uint32_t *>(base + o_ik);
+        d.ci_ik = reinterpret_cast<const int32_t *>(base + o_ik + align_up(4 * (size_t)(vsize(i) + 1)));
+        d.ci_ik_off = col0(i, k);
+        d.rp_jk = reinterpret_cast<const uint32_t *>(base + o_jk);
+        d.ci_jk = reinterpret_cast<const int32_t *>(base + o_jk + align_up(4 * (size_t)(vsize(j) + 1)));
+        d.ci_jk_off = col0(j, k);
+        d.c_i = pl.h_cuts[i];
+        d.c_j = pl.h_cuts[j];
+        d.diag = k == j;
+        d.task = t;
+        if (cudaMemcpyAsync(pl.desc + t, &stage[h][t], sizeof(TaskDesc), cudaMemcpyHostToDevice,
+                            cs) != cudaSuccess) {
+          set_error("streamed count: descriptor copy failed");
+          st = BBTC_ECUDA;
+          break;
+        }
+      }
+      if (st != BBTC_OK) break;
+      cudaEventRecord(c1, cs);
+      if (cudaEventRecord(copy_done[h], cs) != cudaSuccess ||
+          cudaStreamWaitEvent(s, copy_done[h], 0) != cudaSuccess) {
+        st = BBTC_ECUDA;
+        break;
+      }
+      st = count_launch(g, pl, runs[first].item0, runs[pos - 1].item1 - runs[first].item0,
+                        vertex_count, per_graph, timeout_ms, s);
+      if (st != BBTC_OK) break;
+      if (cudaEventRecord(kern_done[h], s) != cudaSuccess) {
+        st = BBTC_ECUDA;
+        break;
+      }
+      used_half[h] = true;
+      ++round;
+      // copy time of this round (host waits only for the copy, not the kernel)
+      if (cudaEventSynchronize(c1) == cudaSuccess) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c0, c1) == cudaSuccess) copy_ms_total += ms;
+      }
+      cudaEventDestroy(c0);
+      cudaEventDestroy(c1);
+    }
+    if (st != BBTC_OK) break;
+    st = count_finish(pl, s);
+    if (st == BBTC_OK && cudaEventRecord(t_end, s) != cudaSuccess) st = BBTC_ECUDA;
+  } while (0);
+  cudaStreamSynchronize(s);
+  if (cs) {
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+  }
+  if (st == BBTC_OK) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t_begin, t_end) == cudaSuccess) stats->total_ms = ms;
+  }
+  stats->rounds = round;
+  stats->copy_ms = copy_ms_total;
+  for (cudaEvent_t e : {copy_done[0], copy_done[1], kern_done[0], kern_done[1], t_begin, t_end})
+    if (e) cudaEventDestroy(e);
+  for (TaskDesc *d : stage)
+    if (d) cudaFreeHost(d);
+  return st;
+}
+
+}  // namespace bbtc
