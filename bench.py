@@ -446,6 +446,9 @@ def main():
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--kernel", default="auto", choices=["auto", "intersect", "hashmap"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--budget-gb", default="0",
+                    help="comma list of device budgets (GB) for the counting step's blocks, "
+                         "streamed from pinned host memory; 0 = resident; one line each")
     ap.add_argument("--serve-rates", default="200,500,1000,2000,5000")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-seeds", type=int, default=4)
@@ -483,6 +486,7 @@ def main():
             dist.barrier()
 
     p = args.p or DEFAULT_P.get(args.workload, 4)
+    budgets = [float(x) for x in str(args.budget_gb).split(",")]
     n, rp, ci = make_graph(args.workload)
     flags = bb.INPUT_SYMMETRIC  # the generator lists every pair under both endpoints
     stream = torch.cuda.Stream()
@@ -493,110 +497,121 @@ def main():
     torch.cuda.synchronize()
     del rp, ci
 
-    def step(device_resident: bool):
-        if device_resident:
-            h = bb.bbtc_graph_create_async(n, d_rp, d_ci, flags, stream)
-        else:
-            h = bb.bbtc_graph_create_async(n, h_rp, h_ci, flags, stream)
-        try:
-            total = bb.bbtc_count(h, bb.make_opts(p=p, kernel=args.kernel, stream=stream))
-            info = bb.bbtc_graph_get_info(h) if device_resident else None
-            tim = bb.bbtc_graph_get_timings(h) if device_resident else None
-        finally:
-            bb.bbtc_graph_destroy(h)
-        return total, info, tim
+    def measure(budget_gb: float, first_line: bool):
+        budget = int(budget_gb * (1 << 30))
+        def step(device_resident: bool):
+            if device_resident:
+                h = bb.bbtc_graph_create_async(n, d_rp, d_ci, flags, stream)
+            else:
+                h = bb.bbtc_graph_create_async(n, h_rp, h_ci, flags, stream)
+            try:
+                total = bb.bbtc_count(h, bb.make_opts(p=p, kernel=args.kernel, stream=stream,
+                                                      device_budget_bytes=budget))
+                info = bb.bbtc_graph_get_info(h) if device_resident else None
+                tim = bb.bbtc_graph_get_timings(h) if device_resident else None
+            finally:
+                bb.bbtc_graph_destroy(h)
+            return total, info, tim
 
-    # warm-up (also validates that every step gives the same count)
-    totals = set()
-    info = None
-    for _ in range(args.warmup):
-        total, info, _ = step(True)
-        totals.add(total)
-    m = info["m"]
-
-    # timed: device-resident inputs
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    count_ms, prep_ms, plan_ms = [], [], []
-    launches0 = bb.bbtc_kernel_launches()
-    with ClockSampler(local_rank) as clocks:
-        barrier()
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            total, _, tim = step(True)
+        # warm-up (also validates that every step gives the same count)
+        totals = set()
+        info = None
+        for _ in range(args.warmup):
+            total, info, _ = step(True)
             totals.add(total)
-            count_ms.append(tim["count_ms"])
-            prep_ms.append(tim["prep_ms"])
-            plan_ms.append(tim["plan_ms"])
-        ev1.record(stream)
-        torch.cuda.synchronize()
+        m = info["m"]
+
+        # timed: device-resident inputs
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        count_ms, prep_ms, plan_ms, stream_info = [], [], [], []
+        launches0 = bb.bbtc_kernel_launches()
+        with ClockSampler(local_rank) as clocks:
+            barrier()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                total, _, tim = step(True)
+                totals.add(total)
+                count_ms.append(tim["count_ms"])
+                prep_ms.append(tim["prep_ms"])
+                plan_ms.append(tim["plan_ms"])
+                stream_info.append({k: tim[k] for k in ("stream_rounds", "stream_h2d_bytes",
+                                                        "stream_copy_ms")})
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        launches = bb.bbtc_kernel_launches() - launches0
+        ms = reduce_max_ms(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
+
+        # timed: host inputs through the same calls (H2D and count D2H inside)
         barrier()
-    launches = bb.bbtc_kernel_launches() - launches0
-    ms = reduce_max_ms(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            total, _, _ = step(False)
+            totals.add(total)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = reduce_max_ms(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+        barrier()
 
-    # timed: host inputs through the same calls (H2D and count D2H inside)
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        total, _, _ = step(False)
-        totals.add(total)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = reduce_max_ms(e0.elapsed_time(e1) / args.steps, dist, "cuda")
-    barrier()
+        if len(totals) != 1:
+            raise SystemExit(f"inconsistent triangle counts across steps: {sorted(totals)}")
 
-    if len(totals) != 1:
-        raise SystemExit(f"inconsistent triangle counts across steps: {sorted(totals)}")
+        if rank == 0:
+            peak, peak_kind = measured_peaks()
+            kms = sum(count_ms) / len(count_ms)
+            wmin = 4 * (m + info["wedges_in"])
+            achieved = wmin / (kms / 1000.0) / 1e9
+            h2d = (n + 1) * 8 + int(h_ci.numel()) * 4
+            line = {
+                "metric": METRIC,
+                "value": replica_throughput(m, world, ms),
+                "unit": UNIT,
+                "n_gpus": world,
+                "steps": args.steps,
+                "warmup": args.warmup,
+                "ms_per_step": ms,
+                "higher_is_better": True,
+                "scaling": "weak",
+                "vs_baseline": None,
+                "dtype": "int32",
+                "data": "synthetic",
+                "config": {
+                    "workload": WORKLOADS.get(args.workload, args.workload), "p": p,
+                    "kernel": args.kernel,
+                    "n": n, "m": m, "triangles": next(iter(totals)),
+                    "input_entries": int(h_ci.numel()),
+                    "l2": "inputs larger than L2 (input CSR %.2f GB, oriented CSR %.2f GB)"
+                          % (h2d / 1e9, (m * 8 + (n + 1) * 8) / 1e9),
+                    "parallelism": "replicas" if world > 1 else "single GPU",
+                    "phase_ms": {"prep": statistics.mean(prep_ms), "plan": statistics.mean(plan_ms),
+                                 "count_kernel": kms},
+                    "device_budget_gb": budget_gb,
+                    "streaming": stream_info[-1] if budget else None,
+                },
+                "e2e": {"value": replica_throughput(m, world, e2e_ms), "unit": UNIT,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak,
+                             "traffic": recorded_traffic(args.workload, p, args.kernel),
+                             "kernel": "k_count (per-task counting, a9)",
+                             "algorithmic_bytes": wmin,
+                             "bytes_formula": "4*(m + sum over oriented edges (u,v) of d+(v))",
+                             "peak_source": f"{peak_kind} hbm_gbs"},
+                "clocks": clocks.summary(),
+                "gpu_launches": launches,
+            }
+            if not args.no_cpu_baseline and first_line:
+                line["cpu_baseline"] = cpu_baseline(1, p)
+            print(json.dumps(line), flush=True)
 
-    if rank == 0:
-        peak, peak_kind = measured_peaks()
-        kms = sum(count_ms) / len(count_ms)
-        wmin = 4 * (m + info["wedges_in"])
-        achieved = wmin / (kms / 1000.0) / 1e9
-        h2d = (n + 1) * 8 + int(h_ci.numel()) * 4
-        line = {
-            "metric": METRIC,
-            "value": replica_throughput(m, world, ms),
-            "unit": UNIT,
-            "n_gpus": world,
-            "steps": args.steps,
-            "warmup": args.warmup,
-            "ms_per_step": ms,
-            "higher_is_better": True,
-            "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": "int32",
-            "data": "synthetic",
-            "config": {
-                "workload": WORKLOADS.get(args.workload, args.workload), "p": p,
-                "kernel": args.kernel,
-                "n": n, "m": m, "triangles": next(iter(totals)),
-                "input_entries": int(h_ci.numel()),
-                "l2": "inputs larger than L2 (input CSR %.2f GB, oriented CSR %.2f GB)"
-                      % (h2d / 1e9, (m * 8 + (n + 1) * 8) / 1e9),
-                "parallelism": "replicas" if world > 1 else "single GPU",
-                "phase_ms": {"prep": statistics.mean(prep_ms), "plan": statistics.mean(plan_ms),
-                             "count_kernel": kms},
-            },
-            "e2e": {"value": replica_throughput(m, world, e2e_ms), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": recorded_traffic(args.workload, p, args.kernel),
-                         "kernel": "k_count (per-task counting, a9)",
-                         "algorithmic_bytes": wmin,
-                         "bytes_formula": "4*(m + sum over oriented edges (u,v) of d+(v))",
-                         "peak_source": f"{peak_kind} hbm_gbs"},
-            "clocks": clocks.summary(),
-            "gpu_launches": launches,
-        }
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(1, p)
-        print(json.dumps(line), flush=True)
+    for idx, budget_gb in enumerate(budgets):
+        measure(budget_gb, idx == 0)
+
     if dist is not None:
         dist.destroy_process_group()
 

@@ -36,19 +36,43 @@ __global__ void k_cuts(const int64_t *__restrict__ rowptr, int64_t n, int p,
   cuts[i] = c;
 }
 
-// In-edge keys: (part(u) << nb) | v for the oriented edge e = (u, v), value e.
+// In-edge keys for the oriented edge e = (u, v). Packed form (when
+// nb + bits(p) <= 32): key ((part(u) << nb | v) << 32) | u, value = the edge's
+// block position, sorted on the upper half only so u rides along. Otherwise
+// key (part(u) << nb) | v, value e.
 __global__ void k_inedge_keys(const int32_t *__restrict__ colidx,
-                              const int32_t *__restrict__ esrc, int64_t m,
-                              const int32_t *__restrict__ cuts_g, int p, int nb,
+                              const int32_t *__restrict__ esrc,
+                              const uint32_t *__restrict__ pos_of_edge, int64_t m,
+                              const int32_t *__restrict__ cuts_g, int p, int nb, bool packed,
                               uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
   __shared__ int32_t cuts[MAXP + 1];
   for (int i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
   __syncthreads();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
        e += (int64_t)gridDim.x * blockDim.x) {
-    int part = part_of_dev(cuts, p, esrc[e]);
-    keys[e] = ((uint64_t)part << nb) | (uint64_t)colidx[e];
-    vals[e] = (uint32_t)e;
+    const int32_t u = esrc[e];
+    const uint64_t group = ((uint64_t)part_of_dev(cuts, p, u) << nb) | (uint64_t)colidx[e];
+    if (packed) {
+      keys[e] = (group << 32) | (uint64_t)(uint32_t)u;
+      vals[e] = pos_of_edge[e];
+    } else {
+      keys[e] = group;
+      vals[e] = (uint32_t)e;
+    }
+  }
+}
+
+__global__ void k_inedge_unpack(const uint64_t *__restrict__ keys,
+                                const uint32_t *__restrict__ vals, int64_t m, int nb,
+                                int32_t *__restrict__ ie_u, int32_t *__restrict__ ie_v,
+                                uint32_t *__restrict__ ie_e) {
+  const uint64_t mask = (1ull << nb) - 1ull;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[x];
+    ie_u[x] = (int32_t)(uint32_t)k;
+    ie_v[x] = (int32_t)((k >> 32) & mask);
+    ie_e[x] = vals[x];
   }
 }
 
@@ -137,12 +161,12 @@ __global__ void k_bcsr_rowptr(const uint64_t *__restrict__ pos, int64_t total,
 
 // boff[i*(p+1)+j] = first in-edge of part i whose destination is >= c_j.
 __global__ void k_block_offsets(const uint64_t *__restrict__ keys, int64_t m,
-                                const int32_t *__restrict__ cuts, int p, int nb,
+                                const int32_t *__restrict__ cuts, int p, int nb, int shift,
                                 int64_t *__restrict__ boff) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= p * (p + 1)) return;
   const int i = idx / (p + 1), j = idx % (p + 1);
-  const uint64_t target = ((uint64_t)i << nb) + (uint64_t)cuts[j];
+  const uint64_t target = (((uint64_t)i << nb) + (uint64_t)cuts[j]) << shift;
   boff[idx] = lower_bound_dev<uint64_t, int64_t>(keys, 0, m, target);
 }
 
@@ -359,19 +383,26 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   PLAN_TRY(dalloc_n(&pl.ie_e, m, s));
   PLAN_TRY(dalloc_n(&pl.boff, (int64_t)p * (p + 1), s));
   const int pbits = ceil_log2_u64((uint64_t)p);
+  const bool packed = nb + pbits <= 32;
+  const int shift = packed ? 32 : 0;
   bool in_alt = false;
   if (m > 0) {
-    k_inedge_keys<<<grid_for(m, 256, 32), 256, 0, s>>>(g->colidx, g->esrc, m, pl.cuts, p, nb,
-                                                        ka, va);
+    k_inedge_keys<<<grid_for(m, 256, 32), 256, 0, s>>>(g->colidx, g->esrc, pos_of_edge, m,
+                                                        pl.cuts, p, nb, packed, ka, va);
     PLAN_TRY(launch_status("build_plan"));
-    PLAN_TRY(radix_sort(ka, kb, va, vb, m, 0, nb + pbits, s, &in_alt));
-    k_inedge_finish<<<grid_for(m, 256, 32), 256, 0, s>>>(in_alt ? kb : ka, in_alt ? vb : va, m,
-                                                          nb, g->esrc, pos_of_edge, pl.ie_u,
-                                                          pl.ie_v, pl.ie_e);
+    PLAN_TRY(radix_sort(ka, kb, va, vb, m, shift, shift + nb + pbits, s, &in_alt));
+    if (packed) {
+      k_inedge_unpack<<<grid_for(m, 256, 32), 256, 0, s>>>(in_alt ? kb : ka, in_alt ? vb : va,
+                                                            m, nb, pl.ie_u, pl.ie_v, pl.ie_e);
+    } else {
+      k_inedge_finish<<<grid_for(m, 256, 32), 256, 0, s>>>(in_alt ? kb : ka, in_alt ? vb : va,
+                                                            m, nb, g->esrc, pos_of_edge, pl.ie_u,
+                                                            pl.ie_v, pl.ie_e);
+    }
     PLAN_TRY(launch_status("build_plan"));
   }
   k_block_offsets<<<(p * (p + 1) + 127) / 128, 128, 0, s>>>(in_alt ? kb : ka, m, pl.cuts, p, nb,
-                                                            pl.boff);
+                                                            shift, pl.boff);
   PLAN_TRY(launch_status("build_plan"));
 
   // a7 + a8: tasks, estimates, order

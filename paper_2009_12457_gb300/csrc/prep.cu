@@ -3,6 +3,8 @@
 //   a2 degree                     (Sec. 2, Sec. 4.1)
 //   a3 order by degree            (Sec. 4.1: non-decreasing degree, ties by id)
 //   a4 orientation                (Sec. 2: N(G,u) = {v : (u,v) in E, u < v})
+#include <limits.h>
+
 #include "graph.cuh"
 #include "primitives.cuh"
 
@@ -251,7 +253,295 @@ __global__ void k_csr_finish(const uint64_t *__restrict__ okeys, int64_t m, int 
   }
 }
 
+// ------------------------------------------------------------------------
+// Symmetric input with sorted rows (every edge listed under both endpoints,
+// each row ascending): the canonical edges of row u are its entries above u,
+// each counted once, so no global sort is needed.
+
+constexpr int SEG_CAP = 2048;  // longest oriented row sorted in shared memory
+
+__device__ __forceinline__ int64_t row_of_first(const int64_t *rowptr, int64_t n, int64_t target,
+                                                int64_t lo_hint, int64_t hi_hint) {
+  int64_t lo = lo_hint, hi = hi_hint;  // rowptr[lo] <= target
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (rowptr[mid] <= target) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int SP_NT = 256;
+constexpr int SP_ITEMS = 8;
+constexpr int SP_TILE = SP_NT * SP_ITEMS;
+
+// Row of the first entry of every tile of SP_TILE entries (and of the last
+// entry, in the final slot): the row windows of the per-entry passes.
+__global__ void k_tile_rows(const int64_t *__restrict__ rowptr, int64_t n, int64_t nnz,
+                            int64_t ntiles, int64_t *__restrict__ rows) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t target = t < ntiles ? t * SP_TILE : nnz - 1;
+    rows[t] = row_of_first(rowptr, n, target, 0, n);
+  }
+}
+
+// Pass over the entries: thread t of a tile owns entries [t*8, t*8+8) and walks
+// their rows forward from one search inside the tile's row window. MODE 0:
+// degree of u += first copies of v != u, flag unsorted rows and out-of-range
+// ids. MODE 1: out-degree at rank(u) += first copies with rank(v) > rank(u).
+// MODE 2: scatter rank(v) into row rank(u) (any order; rows are sorted after).
+template <int MODE>
+__global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ rowptr,
+                                                    const int32_t *__restrict__ colidx, int64_t n,
+                                                    int64_t nnz,
+                                                    const int64_t *__restrict__ tile_rows,
+                                                    int32_t *__restrict__ deg,
+                                                    const int32_t *__restrict__ rank,
+                                                    unsigned long long *__restrict__ dplus,
+                                                    const int64_t *__restrict__ rowptr_o,
+                                                    unsigned int *__restrict__ cursor,
+                                                    int32_t *__restrict__ colidx_o,
+                                                    int32_t *__restrict__ esrc_o,
+                                                    int32_t *__restrict__ err) {
+  const unsigned lane = threadIdx.x & 31u;
+  const int64_t ntiles = (nnz + SP_TILE - 1) / SP_TILE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t t0 = tile * SP_TILE;
+    const int64_t t1 = t0 + SP_TILE < nnz ? t0 + SP_TILE : nnz;
+    const int64_t rlo = tile_rows[tile], rhi = tile_rows[tile + 1];
+    const int64_t first = t0 + (int64_t)threadIdx.x * SP_ITEMS;
+    int64_t u = first < t1 ? row_of_first(rowptr, n, first, rlo, rhi + 1) : rlo;
+    int64_t row_end = rowptr[u + 1];
+    int32_t ru = MODE > 0 ? rank[u] : 0;
+#pragma unroll
+    for (int i = 0; i < SP_ITEMS; ++i) {
+      const int64_t e = first + i;
+      bool head = false;
+      int32_t v = 0;
+      bool first_in_row = false;
+      if (e < t1) {
+        while (e >= row_end) {  // next non-empty row
+          ++u;
+          row_end = rowptr[u + 1];
+          if (MODE > 0) ru = rank[u];
+        }
+        v = colidx[e];
+        first_in_row = e == rowptr[u];
+        const int32_t prev = first_in_row ? -1 : colidx[e - 1];
+        if (MODE == 0) {
+          if (v < 0 || v >= n) atomicOr(err, 2);
+          else if (!first_in_row && prev > v) atomicOr(err, 4);
+        }
+        head = v >= 0 && v < n && v != u && (first_in_row || prev != v);
+      }
+      if (MODE == 0) {
+        const int64_t key = head ? u : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&deg[key], __popc(peers));
+      } else {
+        const bool up = head && rank[v] > ru;
+        const int64_t key = up ? (int64_t)ru : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        if (MODE == 1) {
+          if (key >= 0 && (int)lane == leader)
+            atomicAdd(&dplus[key], (unsigned long long)__popc(peers));
+        } else {
+          unsigned base = 0;
+          if (key >= 0 && (int)lane == leader) base = atomicAdd(&cursor[key], (unsigned)__popc(peers));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (key >= 0) {
+            const int64_t pos = rowptr_o[key] + base + __popc(peers & ((1u << lane) - 1u));
+            colidx_o[pos] = rank[v];
+            esrc_o[pos] = (int32_t)key;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Oriented keys from the scattered (source, destination) pairs, for graphs
+// with rows too long for k_sort_rows: one global sort orders them instead.
+__global__ void k_pair_keys(const int32_t *__restrict__ esrc, const int32_t *__restrict__ colidx,
+                            int64_t m, int nb, uint64_t *__restrict__ keys) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    keys[e] = ((uint64_t)esrc[e] << nb) | (uint64_t)colidx[e];
+}
+
+__global__ void k_pair_unkey(const uint64_t *__restrict__ keys, int64_t m, int nb,
+                             int32_t *__restrict__ colidx) {
+  const uint64_t mask = (1ull << nb) - 1ull;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    colidx[e] = (int32_t)(keys[e] & mask);
+}
+
+// Sort every oriented row ascending: one warp per row, rows of up to 32 in
+// registers (bitonic network over shuffles), longer rows (up to SEG_CAP) in the
+// warp's shared memory (bitonic network, padded to a power of two).
+constexpr int SR_WARPS = 4;
+
+__global__ void __launch_bounds__(SR_WARPS * 32) k_sort_rows(const int64_t *__restrict__ rowptr,
+                                                             int64_t n,
+                                                             int32_t *__restrict__ colidx) {
+  __shared__ int32_t buf[SR_WARPS][SEG_CAP];
+  const unsigned lane = threadIdx.x & 31u;
+  const int warp = threadIdx.x >> 5;
+  int32_t *sm = buf[warp];
+  const int64_t nwarps = (int64_t)gridDim.x * SR_WARPS;
+  for (int64_t r = (int64_t)blockIdx.x * SR_WARPS + warp; r < n; r += nwarps) {
+    const int64_t b = rowptr[r];
+    const int len = (int)(rowptr[r + 1] - b);
+    if (len <= 1) continue;
+    if (len <= 32) {
+      int32_t x = (int)lane < len ? colidx[b + lane] : INT_MAX;
+      for (int k = 2; k <= 32; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+          const bool up = ((lane & k) == 0);
+          const bool lower = (lane & j) == 0;
+          x = (lower == up) ? min(x, y) : max(x, y);
+        }
+      if ((int)lane < len) colidx[b + lane] = x;
+    } else {
+      int size = 64;
+      while (size < len) size <<= 1;
+      for (int i = lane; i < size; i += 32) sm[i] = i < len ? colidx[b + i] : INT_MAX;
+      __syncwarp();
+      for (int k = 2; k <= size; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = lane; i < size; i += 32) {
+            const int l = i ^ j;
+            if (l > i) {
+              const int32_t a = sm[i], c = sm[l];
+              const bool up = (i & k) == 0;
+              if ((a > c) == up) {
+                sm[i] = c;
+                sm[l] = a;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      for (int i = lane; i < len; i += 32) colidx[b + i] = sm[i];
+      __syncwarp();
+    }
+  }
+}
+
 }  // namespace
+
+// a1-a4 for symmetric input with sorted rows. Sets *applied = false (and does
+// nothing lasting) when some row turns out unsorted.
+static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
+                                      const int32_t *d_colidx, int64_t nnz, int32_t *err,
+                                      bool *applied) {
+  cudaStream_t s = g->stream;
+  const int64_t n = g->n;
+  const int nb = g->nb;
+  *applied = false;
+  Scratch scratch(s);
+  BBTC_TRY(dalloc_n(&g->deg, n, s));
+  g->bytes += (uint64_t)(n > 0 ? n : 1) * sizeof(int32_t);
+  BBTC_CUDA(cudaMemsetAsync(g->deg, 0, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s));
+  const int64_t ntiles = (nnz + SP_TILE - 1) / SP_TILE;
+  int64_t *tile_rows = nullptr;
+  BBTC_TRY(scratch.get(&tile_rows, ntiles + 1));
+  k_tile_rows<<<grid_for(ntiles + 1, 256, 16), 256, 0, s>>>(d_rowptr, n, nnz, ntiles, tile_rows);
+  BBTC_LAUNCH_CHECK();
+  const unsigned grid = grid_for(ntiles, 1, 32);
+  k_sym_pass<0><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, g->deg, nullptr,
+                                       nullptr, nullptr, nullptr, nullptr, nullptr, err);
+  BBTC_LAUNCH_CHECK();
+  int32_t herr = 0;
+  BBTC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  if (herr & 1) {
+    set_error("bbtc_graph_create: rowptr[0] != 0 or rowptr decreases");
+    return BBTC_EINVAL;
+  }
+  if (herr & 2) {
+    set_error("bbtc_graph_create: colidx entry outside [0, n)");
+    return BBTC_EINVAL;
+  }
+  if (herr & 4) return BBTC_OK;  // unsorted rows: the general path takes over
+  *applied = true;
+
+  // a3: order by (degree, id)
+  int32_t *rank = nullptr, *dmax = nullptr;
+  uint64_t *rk = nullptr, *rk_alt = nullptr;
+  BBTC_TRY(scratch.get(&rank, n));
+  BBTC_TRY(scratch.get(&dmax, 1));
+  BBTC_TRY(scratch.get(&rk, n));
+  BBTC_TRY(scratch.get(&rk_alt, n));
+  BBTC_TRY(dalloc_n(&g->perm, n, s));
+  g->bytes += (uint64_t)n * sizeof(int32_t);
+  BBTC_TRY(reduce_max_i32(g->deg, n, dmax, s));
+  int32_t hdmax = 0;
+  BBTC_CUDA(cudaMemcpyAsync(&hdmax, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  g->deg_max = hdmax;
+  k_rank_keys<<<grid_for(n, 256, 16), 256, 0, s>>>(g->deg, n, nb, rk);
+  BBTC_LAUNCH_CHECK();
+  bool in_alt = false;
+  BBTC_TRY(radix_sort(rk, rk_alt, nullptr, nullptr, n, 0, nb + ceil_log2_u64((uint64_t)hdmax + 1),
+                      s, &in_alt));
+  k_rank_finish<<<grid_for(n, 256, 16), 256, 0, s>>>(in_alt ? rk_alt : rk, n, nb, g->perm, rank);
+  BBTC_LAUNCH_CHECK();
+
+  // a4: out-degrees by rank, offsets, scatter, per-row sort
+  BBTC_TRY(dalloc_n(&g->rowptr, n + 1, s));
+  g->bytes += (uint64_t)(n + 1) * 8;
+  BBTC_CUDA(cudaMemsetAsync(g->rowptr, 0, sizeof(int64_t) * (size_t)(n + 1), s));
+  k_sym_pass<1><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, nullptr, rank,
+                                       reinterpret_cast<unsigned long long *>(g->rowptr),
+                                       nullptr, nullptr, nullptr, nullptr, err);
+  BBTC_LAUNCH_CHECK();
+  int64_t *stats = nullptr;
+  BBTC_TRY(scratch.get(&stats, 2));
+  BBTC_TRY(reduce_max_i64(g->rowptr, n, &stats[0], s));
+  BBTC_TRY(exclusive_scan_u64(reinterpret_cast<uint64_t *>(g->rowptr),
+                              reinterpret_cast<uint64_t *>(g->rowptr), n + 1, s));
+  int64_t h[2] = {0, 0};
+  BBTC_CUDA(cudaMemcpyAsync(&h[0], &stats[0], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaMemcpyAsync(&h[1], g->rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  g->dplus_max = h[0];
+  const int64_t m = h[1];
+  if (m > 0xFFFFFFFFLL) {
+    set_error("bbtc_graph_create: %lld simple edges exceed 2^32 - 1", (long long)m);
+    return BBTC_EINVAL;
+  }
+  g->m = m;
+  BBTC_TRY(dalloc_n(&g->colidx, m, s));
+  BBTC_TRY(dalloc_n(&g->esrc, m, s));
+  g->bytes += (uint64_t)(m > 0 ? m : 1) * 8;
+  unsigned int *cursor = nullptr;
+  BBTC_TRY(scratch.get(&cursor, n));
+  BBTC_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned int) * (size_t)(n > 0 ? n : 1), s));
+  k_sym_pass<2><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, nullptr, rank,
+                                       nullptr, g->rowptr, cursor, g->colidx, g->esrc, err);
+  BBTC_LAUNCH_CHECK();
+  if (m > 0) {
+    if (g->dplus_max <= SEG_CAP) {
+      k_sort_rows<<<grid_for(n, SR_WARPS, 64), SR_WARPS * 32, 0, s>>>(g->rowptr, n, g->colidx);
+      BBTC_LAUNCH_CHECK();
+    } else {
+      uint64_t *ok = nullptr, *ok_alt = nullptr;
+      BBTC_TRY(scratch.get(&ok, m));
+      BBTC_TRY(scratch.get(&ok_alt, m));
+      k_pair_keys<<<grid_for(m, 256, 32), 256, 0, s>>>(g->esrc, g->colidx, m, nb, ok);
+      BBTC_LAUNCH_CHECK();
+      BBTC_TRY(radix_sort(ok, ok_alt, nullptr, nullptr, m, 0, 2 * nb, s, &in_alt));
+      k_pair_unkey<<<grid_for(m, 256, 32), 256, 0, s>>>(in_alt ? ok_alt : ok, m, nb, g->colidx);
+      BBTC_LAUNCH_CHECK();
+    }
+  }
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  return BBTC_OK;
+}
 
 bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t *d_colidx,
                           int64_t nnz, bool symmetric) {
@@ -270,6 +560,14 @@ bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t 
   if (n > 0) {
     k_validate_rowptr<<<grid_for(n, 256, 8), 256, 0, s>>>(d_rowptr, n, err);
     BBTC_LAUNCH_CHECK();
+  }
+
+  // ---- symmetric input with sorted rows: per-row path, no global sort
+  if (symmetric && !g->voff && nnz > 0) {
+    bool applied = false;
+    BBTC_TRY(prepare_sym_sorted(g, d_rowptr, d_colidx, nnz, err, &applied));
+    if (applied) return BBTC_OK;
+    BBTC_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));  // fall through: general path
   }
 
   // ---- a1: canonical keys (compacted), sort, unique; a2: degree
@@ -324,8 +622,10 @@ bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t 
   uint64_t *sorted = in_alt ? kb : ka;
   uint64_t *ukeys = in_alt ? ka : kb;
 
-  BBTC_TRY(dalloc_n(&g->deg, n, s));
-  g->bytes += (uint64_t)(n > 0 ? n : 1) * sizeof(int32_t);
+  if (!g->deg) {
+    BBTC_TRY(dalloc_n(&g->deg, n, s));
+    g->bytes += (uint64_t)(n > 0 ? n : 1) * sizeof(int32_t);
+  }
   BBTC_CUDA(cudaMemsetAsync(g->deg, 0, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s));
   int64_t m = 0;
   if (nkeys > 0) {

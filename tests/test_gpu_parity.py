@@ -192,3 +192,33 @@ def test_invalid_inputs_are_rejected():
         with pytest.raises(bb.BbtcError):
             dev.count(p=-1)
         assert dev.count(p=2) == 4  # the handle still works after a rejected call
+
+
+def test_symmetric_fast_path_matches_general_path():
+    """Symmetric sorted rows take the per-row path; unsorted rows and the
+    general path must give the byte-identical oriented CSR."""
+    rng = np.random.default_rng(31)
+    for n, rp, ci in (graphgen.rmat(13, 16, 8), graphgen.gnm(3000, 20000, 9),
+                      pins.with_noise(*G.gnp(90, 0.2, rng), rng)):
+        sym_sorted = (n, rp, np.concatenate([np.sort(ci[rp[v]:rp[v + 1]]) for v in range(n)]
+                                            or [np.zeros(0, np.int32)]).astype(np.int32))
+        shuffled = (n, rp, ci.copy())
+        for v in range(n):
+            rng.shuffle(shuffled[2][rp[v]:rp[v + 1]])
+        ref = oracle.prepare(n, rp, ci)
+        for g, sym in ((sym_sorted, True), (shuffled, True), ((n, rp, ci), False)):
+            with bb.Graph(*g, symmetric=sym) as dev:
+                ori = dev.oriented()
+                assert np.array_equal(ori["rowptr"], ref["rowptr"])
+                assert np.array_equal(ori["colidx"], ref["colidx"])
+                assert np.array_equal(ori["perm"], ref["perm"])
+                assert np.array_equal(ori["degree"], ref["deg"])
+                assert dev.info()["dplus_max"] == int(np.diff(ref["rowptr"]).max(initial=0))
+
+
+def test_rows_longer_than_the_shared_sort():
+    # K_2100: equal degrees, ties by id, so vertex 0 has 2099 out-neighbours
+    k = 2100
+    with bb.Graph(*G.complete(k), symmetric=True) as dev:
+        assert dev.info()["dplus_max"] == k - 1
+        assert dev.count(p=3) == G.choose(k, 3)
