@@ -91,7 +91,7 @@ struct LaneRec {
 constexpr int UNIFORM_MIN = 4;  // a run of >= 4 in-edges into one v is a uniform batch
 
 template <int MODE>
-__global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
+__global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
   constexpr bool PER_VERTEX = (MODE & MODE_VERTEX) != 0;
   constexpr bool PER_GRAPH = (MODE & MODE_GRAPH) != 0;
   extern __shared__ __align__(16) unsigned char count_smem_raw[];
@@ -249,43 +249,53 @@ __global__ void __launch_bounds__(CT_NT) k_count(CountParams P) {
       unsigned long long batch_hits = 0;  // one graph per uniform batch
       int o = 0;
       uint32_t o_end = rec.incl[0];
-      int64_t addr = rec.s0[0];  // colidx index of probe q is addr + q
-      int64_t lo = b0, hi = b1;
-      if (!uniform) {
-        lo = rec.b0[0];
-        hi = rec.b1[0];
-      }
-      for (uint32_t q = lane; q < total; q += 32) {
-        while (q >= o_end) {
-          ++o;
-          const uint32_t prev_end = o_end;
-          o_end = rec.incl[o];
-          addr = rec.s0[o] - (int64_t)prev_end;
-          if (!uniform) {
-            lo = rec.b0[o];
-            hi = rec.b1[o];
+      int64_t addr = rec.s0[0];  // ci_ik index of probe q is addr + q
+      // four probes per lane per round: their loads are issued before any
+      // lookup, so each lane keeps four global loads in flight
+      constexpr int U = 4;
+      for (uint32_t qb = lane; qb < total; qb += 32 * U) {
+        int32_t wv[U];
+        int own[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+          const uint32_t q = qb + 32u * r;
+          own[r] = -1;
+          if (q < total) {
+            while (q >= o_end) {
+              ++o;
+              const uint32_t prev_end = o_end;
+              o_end = rec.incl[o];
+              addr = rec.s0[o] - (int64_t)prev_end;
+            }
+            wv[r] = ci_ik[addr + q];
+            own[r] = o;
           }
         }
-        const int32_t wv = ci_ik[addr + q];
-        bool hit;
-        if (staged) {
-          hit = staged_hash ? hash_contains(stage, staged_log2h, wv)
-                            : sorted_contains(stage, staged_len, wv);
-        } else {
-          const int64_t pos = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, wv);
-          hit = pos < hi && ci_jk[pos] == wv;
-        }
-        if (hit) {
-          ++acc;
-          if (PER_VERTEX) {
-            atomicAdd(&P.vcount[rec.u[o]], 1ull);
-            atomicAdd(&P.vcount[rec.v[o]], 1ull);
-            atomicAdd(&P.vcount[wv], 1ull);
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+          if (own[r] < 0) continue;
+          bool hit;
+          if (staged) {
+            hit = staged_hash ? hash_contains(stage, staged_log2h, wv[r])
+                              : sorted_contains(stage, staged_len, wv[r]);
+          } else {
+            const int64_t lo = uniform ? b0 : rec.b0[own[r]];
+            const int64_t hi = uniform ? b1 : rec.b1[own[r]];
+            const int64_t pos = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, wv[r]);
+            hit = pos < hi && ci_jk[pos] == wv[r];
           }
-          if (PER_GRAPH) {
-            // every in-edge into v comes from v's own graph
-            if (uniform) ++batch_hits;
-            else atomicAdd(&P.graph_count[P.gid[rec.v[o]]], 1ull);
+          if (hit) {
+            ++acc;
+            if (PER_VERTEX) {
+              atomicAdd(&P.vcount[rec.u[own[r]]], 1ull);
+              atomicAdd(&P.vcount[rec.v[own[r]]], 1ull);
+              atomicAdd(&P.vcount[wv[r]], 1ull);
+            }
+            if (PER_GRAPH) {
+              // every in-edge into v comes from v's own graph
+              if (uniform) ++batch_hits;
+              else atomicAdd(&P.graph_count[P.gid[rec.v[own[r]]]], 1ull);
+            }
           }
         }
       }
