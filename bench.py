@@ -206,7 +206,7 @@ def reference_arm(args, rank: int, world: int):
         return
     steps_total = args.steps + args.warmup
     scale = oracle_sample_scale(steps_total)
-    p = args.p or DEFAULT_P.get(args.workload, 4)
+    p = int(str(args.p).split(",")[0]) or DEFAULT_P.get(args.workload, 4)
     for _ in range(args.warmup):
         run_oracle_sample(scale, p)
     times, m = [], 0
@@ -401,7 +401,8 @@ def run_serve(args, world, rank, local_rank):
 
     # serial baseline on the first requests
     nser = min(args.serve_serial, len(keys_all))
-    _, serial_gps = serve.serial_baseline(source, keys_all[:nser], symmetric=True, p=args.p)
+    serve_p = int(str(args.p).split(",")[0])
+    _, serial_gps = serve.serial_baseline(source, keys_all[:nser], symmetric=True, p=serve_p)
     results = []
     offset = 0
     for lam in rates:
@@ -409,7 +410,7 @@ def run_serve(args, world, rank, local_rank):
         keys = keys_all[offset:offset + len(arrivals)]
         offset += len(arrivals)
         srv = serve.Server(source, device_budget_bytes=int(args.serve_budget_gb * (1 << 30)),
-                           max_batch=256, workers=2, p=args.p, symmetric=True)
+                           max_batch=256, workers=2, p=serve_p, symmetric=True)
         try:
             reqs = serve.run_open_loop(srv, keys, arrivals)
         finally:
@@ -425,7 +426,7 @@ def run_serve(args, world, rank, local_rank):
         "higher_is_better": True, "data": "synthetic",
         "config": {"workload": "serving: Poisson arrivals, R-MAT scales 10-22, edge factor 16",
                    "seconds_per_rate": args.serve_seconds, "seed_pool_per_scale": seeds,
-                   "device_cache_budget_gb": args.serve_budget_gb, "p": args.p,
+                   "device_cache_budget_gb": args.serve_budget_gb, "p": serve_p,
                    "host_generation_s": gen_s},
         "serial_plain_graphs_per_s": serial_gps,
         "rates": results,
@@ -443,7 +444,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat-s23",
                     help="rmat-s23 (default), rmat-s14, chunglu-friendster, or rmat-sNN")
-    ap.add_argument("--p", type=int, default=0)
+    ap.add_argument("--p", default="0", help="blocks per side; a comma list runs each")
     ap.add_argument("--kernel", default="auto", choices=["auto", "intersect", "hashmap"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--budget-gb", default="0",
@@ -485,7 +486,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    p = args.p or DEFAULT_P.get(args.workload, 4)
+    p_list = [int(x) for x in str(args.p).split(",")]
+    p_list = [q or DEFAULT_P.get(args.workload, 4) for q in p_list]
     budgets = [float(x) for x in str(args.budget_gb).split(",")]
     n, rp, ci = make_graph(args.workload)
     flags = bb.INPUT_SYMMETRIC  # the generator lists every pair under both endpoints
@@ -497,7 +499,7 @@ def main():
     torch.cuda.synchronize()
     del rp, ci
 
-    def measure(budget_gb: float, first_line: bool):
+    def measure(p: int, budget_gb: float, first_line: bool):
         budget = int(budget_gb * (1 << 30))
         def step(device_resident: bool):
             if device_resident:
@@ -609,8 +611,17 @@ def main():
                 line["cpu_baseline"] = cpu_baseline(1, p)
             print(json.dumps(line), flush=True)
 
-    for idx, budget_gb in enumerate(budgets):
-        measure(budget_gb, idx == 0)
+    first = True
+    for p in p_list:
+        for budget_gb in budgets:
+            try:
+                measure(p, budget_gb, first)
+            except bb.BbtcError as e:  # e.g. a budget too small for one task's blocks
+                if rank == 0:
+                    print(json.dumps({"metric": METRIC, "error": str(e), "p": p,
+                                      "device_budget_gb": budget_gb,
+                                      "workload": args.workload}), flush=True)
+            first = False
 
     if dist is not None:
         dist.destroy_process_group()

@@ -250,9 +250,9 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
       int o = 0;
       uint32_t o_end = rec.incl[0];
       int64_t addr = rec.s0[0];  // ci_ik index of probe q is addr + q
-      // four probes per lane per round: their loads are issued before any
-      // lookup, so each lane keeps four global loads in flight
-      constexpr int U = 4;
+      // U probes per lane per round: their loads are issued before any
+      // lookup, so each lane keeps U global loads in flight
+      constexpr int U = 8;
       for (uint32_t qb = lane; qb < total; qb += 32 * U) {
         int32_t wv[U];
         int own[U];

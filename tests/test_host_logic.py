@@ -1,0 +1,48 @@
+"""Host-side logic of the serving loop and the autotuner (no GPU)."""
+import json
+
+import numpy as np
+
+from paper_2009_12457_gb300 import autotune, serve
+
+
+def test_poisson_trace_is_seeded_and_has_the_right_rate():
+    a = serve.poisson_trace(1000.0, 5.0, seed=5)
+    b = serve.poisson_trace(1000.0, 5.0, seed=5)
+    assert np.array_equal(a, b)
+    assert np.all(np.diff(a) > 0) and a[-1] < 5.0
+    assert abs(len(a) - 5000) < 5 * np.sqrt(5000)  # within 5 sigma of the mean
+    assert not np.array_equal(a, serve.poisson_trace(1000.0, 5.0, seed=6))
+
+
+def test_latency_summary():
+    reqs = []
+    for i in range(100):
+        r = serve.Request(i, ("g", i % 3), arrival=float(i))
+        r.finish = float(i) + 0.001 * (i + 1)
+        r.batch_size = 1 + i % 4
+        reqs.append(r)
+    s = serve.latency_summary(reqs)
+    assert abs(s["p50_ms"] - 50.5) < 1.0
+    assert abs(s["p99_ms"] - 99.0) < 1.5
+    assert s["requests"] == 100 and s["mean_batch"] == 2.5
+    assert abs(s["graphs_per_s"] - 100 / (99.1 - 0.0)) < 1e-6
+
+
+def test_size_classes_group_similar_graphs():
+    a = autotune.size_class({"n": 1 << 20, "m": 16 << 20})
+    b = autotune.size_class({"n": (1 << 20) + 5, "m": (16 << 20) + 999})
+    c = autotune.size_class({"n": 1 << 20, "m": 64 << 20})
+    assert a == b and a != c
+
+
+def test_autotuner_cache_round_trip(tmp_path):
+    path = tmp_path / "t.json"
+    t = autotune.Autotuner(cache_path=str(path))
+    t.cache["m2^20_d2^5"] = {"p": 4, "kernel": "hashmap", "hash_threshold": 0, "chunk": 256,
+                              "count_ms": 1.0}
+    t._save()
+    again = autotune.Autotuner(cache_path=str(path))
+    assert again.cache == json.loads(path.read_text())
+    opts = autotune.Autotuner.opts(again.cache["m2^20_d2^5"])
+    assert opts.p == 4 and opts.kernel == 2 and opts.chunk == 256
