@@ -78,6 +78,10 @@ typedef struct {
                                    (bbtc_graph_create_batch / bbtc_count_batch) */
   int32_t chunk;                /* in-edges per work item of the counting kernel; 0 = auto */
   int32_t reserved;             /* must be 0 */
+  uint64_t *per_task_cycles_out; /* NULL, or bbtc_num_tasks(p) uint64 in Alg. 4 order: SM
+                                    clock cycles the counting kernel's warps spent on each
+                                    task's work items (the measured side of the Sec. 5
+                                    workload estimate) */
 } bbtc_opts;
 
 #define BBTC_OUT_DEVICE 0x1u

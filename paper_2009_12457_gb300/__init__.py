@@ -57,6 +57,7 @@ class bbtc_opts(ctypes.Structure):
         ("per_graph_out", ctypes.c_void_p),
         ("chunk", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("per_task_cycles_out", ctypes.c_void_p),
     ]
 
 
@@ -211,7 +212,7 @@ def bbtc_graph_destroy(handle: int) -> None:
 def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
               device_budget_bytes: int = 0, per_vertex_out=None, per_task_out=None,
               stream=None, hash_threshold: int = 0, per_graph_out=None,
-              chunk: int = 0) -> bbtc_opts:
+              chunk: int = 0, per_task_cycles_out=None) -> bbtc_opts:
     o = bbtc_opts_init()
     o.p = p
     o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
@@ -219,13 +220,15 @@ def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
     o.device_budget_bytes = device_budget_bytes
     o.hash_threshold = hash_threshold
     o.chunk = chunk
-    outs = [(_ptr(a), a is not None) for a in (per_vertex_out, per_task_out, per_graph_out)]
+    outs = [(_ptr(a), a is not None)
+            for a in (per_vertex_out, per_task_out, per_graph_out, per_task_cycles_out)]
     kinds = {dev for (addr, dev), given in outs if given}
     if len(kinds) > 1:
         raise ValueError("optional outputs must all be host arrays or all device arrays")
     o.per_vertex_out = outs[0][0][0] or None
     o.per_task_out = outs[1][0][0] or None
     o.per_graph_out = outs[2][0][0] or None
+    o.per_task_cycles_out = outs[3][0][0] or None
     o.flags = OUT_DEVICE if kinds == {True} else 0
     o.stream = _stream_ptr(stream) or None
     return o
@@ -335,18 +338,23 @@ class Graph:
 
     def count(self, p: int = 0, kernel: str = "auto", per_vertex: bool = False,
               per_task: bool = False, timeout_ms: int = 0, device_budget_bytes: int = 0,
-              stream=None, hash_threshold: int = 0, per_graph: bool = False, chunk: int = 0):
-        """Total triangle count, or a dict with per-task / per-vertex / per-graph counts."""
+              stream=None, hash_threshold: int = 0, per_graph: bool = False, chunk: int = 0,
+              per_task_cycles: bool = False):
+        """Total triangle count, or a dict with per-task / per-vertex / per-graph counts
+        (and, with per_task_cycles, the SM cycles spent on each task)."""
         pt = np.zeros(max(bbtc_num_tasks(p), 1), dtype=np.uint64) if per_task and p > 0 else None
         if per_task and p == 0:
             raise ValueError("per_task needs an explicit p")
         pv = np.zeros(max(self.n, 1), dtype=np.uint64) if per_vertex else None
         ng = self.info()["num_graphs"] if per_graph else 0
         pg = np.zeros(max(ng, 1), dtype=np.uint64) if per_graph else None
+        if per_task_cycles and p == 0:
+            raise ValueError("per_task_cycles needs an explicit p")
+        cyc = np.zeros(max(bbtc_num_tasks(p), 1), dtype=np.uint64) if per_task_cycles else None
         opts = make_opts(p, kernel, timeout_ms, device_budget_bytes, pv, pt, stream,
-                         hash_threshold, pg, chunk)
+                         hash_threshold, pg, chunk, cyc)
         total = bbtc_count(self.handle, opts)
-        if not per_task and not per_vertex and not per_graph:
+        if not per_task and not per_vertex and not per_graph and not per_task_cycles:
             return total
         out = {"total": total}
         if per_task:
@@ -355,6 +363,8 @@ class Graph:
             out["per_vertex"] = pv[:self.n]
         if per_graph:
             out["per_graph"] = pg[:ng]
+        if per_task_cycles:
+            out["per_task_cycles"] = cyc[:bbtc_num_tasks(p)]
         return out
 
     def info(self) -> dict:

@@ -364,17 +364,23 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   Scratch scratch(s);
   unsigned long long *vertex_count = nullptr;
   if (opts.per_vertex_out) BBTC_TRY(scratch.get(&vertex_count, g->n));
+  unsigned long long *task_cycles = nullptr;
+  if (opts.per_task_cycles_out) {
+    BBTC_TRY(scratch.get(&task_cycles, pl.ntasks));
+    BBTC_CUDA(cudaMemsetAsync(task_cycles, 0, sizeof(uint64_t) * (size_t)pl.ntasks, s));
+  }
   const bool per_graph = opts.per_graph_out != nullptr;
   if (budgeted) {
     StreamStats st;
     BBTC_TRY(run_count_streamed(g, g->plan, opts.device_budget_bytes, vertex_count, per_graph,
-                                opts.timeout_ms, s, &st));
+                                opts.timeout_ms, s, &st, task_cycles));
     g->stream_stats.rounds = st.rounds;
     g->stream_stats.h2d_bytes = st.h2d_bytes;
     g->stream_stats.copy_ms = st.copy_ms;
     g->stream_stats_total_ms = st.total_ms;
   } else {
-    BBTC_TRY(run_count(g, pl, vertex_count, per_graph, opts.timeout_ms, s, g->ev[4], g->ev[5]));
+    BBTC_TRY(run_count(g, pl, vertex_count, per_graph, opts.timeout_ms, s, g->ev[4], g->ev[5],
+                       task_cycles));
     g->stream_stats_total_ms = -1.0;
   }
   unsigned long long head[SCR_TASKS] = {0, 0, 0};
@@ -392,6 +398,9 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   if (per_graph)
     BBTC_CUDA(cudaMemcpyAsync(opts.per_graph_out, pl.scratch + SCR_TASKS + pl.ntasks,
                               sizeof(uint64_t) * (size_t)g->ng, kind, s));
+  if (task_cycles)
+    BBTC_CUDA(cudaMemcpyAsync(opts.per_task_cycles_out, task_cycles,
+                              sizeof(uint64_t) * (size_t)pl.ntasks, kind, s));
   if (opts.per_vertex_out && g->n > 0) {
     unsigned long long *by_id = nullptr;
     BBTC_TRY(scratch.get(&by_id, g->n));
@@ -421,10 +430,10 @@ bbtc_status bbtc_count_async(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t 
               "with bbtc_count (without a device budget) or bbtc_graph_get_plan first");
     return BBTC_EINVAL;
   }
-  if (opts.per_vertex_out ||
+  if (opts.per_vertex_out || opts.per_task_cycles_out ||
       ((opts.per_task_out || opts.per_graph_out) && !(opts.flags & BBTC_OUT_DEVICE))) {
     set_error("bbtc_count_async: outputs must be device pointers (BBTC_OUT_DEVICE) and "
-              "per_vertex_out must be NULL");
+              "per_vertex_out / per_task_cycles_out must be NULL");
     return BBTC_EINVAL;
   }
   DeviceGuard dg(g->device);
@@ -489,6 +498,7 @@ bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts
       bbtc_opts uo = o;
       uo.per_task_out = nullptr;
       uo.per_vertex_out = nullptr;
+      uo.per_task_cycles_out = nullptr;
       uo.per_graph_out = sub;
       uo.flags = 0;
       uo.stream = s;

@@ -30,6 +30,7 @@ struct CountParams {
   unsigned long long *vcount;       // per-vertex counts by position (MODE & 1)
   const int32_t *gid;               // graph of each position (MODE & 2)
   unsigned long long *graph_count;  // per-graph counts (MODE & 2)
+  unsigned long long *task_cycles;  // nullable: SM cycles spent on each task's items
   int32_t *status;
   uint64_t timeout_ns;
 };
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
     }
     const WorkItem w = P.items[it];
     const int t = w.task;
+    const long long t_item = P.task_cycles ? clock64() : 0;
     const bool use_hash = (w.flags & 1) != 0;
     const TaskDesc &d = P.desc[t];
     // block arrays are indexed locally: in-edge x at [x - ie_off], column
@@ -307,6 +309,8 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
     }
     acc = warp_sum(acc);
     if (lane == 0 && acc) atomicAdd(&P.task_count[t], acc);
+    if (P.task_cycles && lane == 0)
+      atomicAdd(&P.task_cycles[t], (unsigned long long)(clock64() - t_item));
   }
 }
 
@@ -399,7 +403,7 @@ bbtc_status count_reset(bbtc_graph *g, const Plan &pl, unsigned long long *verte
 
 bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t nitems,
                          unsigned long long *vertex_count, bool per_graph, uint32_t timeout_ms,
-                         cudaStream_t s) {
+                         cudaStream_t s, unsigned long long *task_cycles) {
   if (nitems <= 0) return BBTC_OK;
   unsigned long long *scr = pl.scratch;
   BBTC_CUDA(cudaMemsetAsync(scr + SCR_HEAD, 0, sizeof(unsigned long long), s));
@@ -414,6 +418,7 @@ bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t n
   P.graph_count = scr + SCR_TASKS + pl.ntasks;
   P.status = reinterpret_cast<int32_t *>(scr + SCR_STATUS);
   P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
+  P.task_cycles = task_cycles;
   const int mode = (vertex_count ? MODE_VERTEX : 0) | (per_graph ? MODE_GRAPH : 0);
   int64_t blocks = (int64_t)num_sms() * pl.blocks_per_sm[mode];
   const int64_t need = (nitems + CT_NT / 32 - 1) / (CT_NT / 32);
@@ -438,10 +443,12 @@ bbtc_status count_finish(const Plan &pl, cudaStream_t s) {
 
 bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                       bool per_graph, uint32_t timeout_ms, cudaStream_t s,
-                      cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+                      cudaEvent_t ev_begin, cudaEvent_t ev_end,
+                      unsigned long long *task_cycles) {
   BBTC_TRY(count_reset(g, pl, vertex_count, per_graph, s));
   if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
-  BBTC_TRY(count_launch(g, pl, 0, pl.nitems, vertex_count, per_graph, timeout_ms, s));
+  BBTC_TRY(count_launch(g, pl, 0, pl.nitems, vertex_count, per_graph, timeout_ms, s,
+                        task_cycles));
   if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
   return count_finish(pl, s);
 }
@@ -537,6 +544,7 @@ extern "C" bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *c
       P.vcount = nullptr;
       P.gid = nullptr;
       P.graph_count = nullptr;
+      P.task_cycles = nullptr;
       P.status = reinterpret_cast<int32_t *>(scratch + NOALLOC_STATUS);
       P.timeout_ns = 0;
       const size_t smem = count_smem_bytes();

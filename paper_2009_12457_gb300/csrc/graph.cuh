@@ -143,14 +143,15 @@ bbtc_status configure_count_kernels(Plan *pl);
 // scratch); the total goes to the plan scratch. Enqueues only.
 bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                       bool per_graph, uint32_t timeout_ms, cudaStream_t s,
-                      cudaEvent_t ev_begin, cudaEvent_t ev_end);
+                      cudaEvent_t ev_begin, cudaEvent_t ev_end,
+                      unsigned long long *task_cycles = nullptr);
 // The three parts of run_count: zero the outputs, drain items [item0,
 // item0 + nitems) in one persistent launch (accumulating), sum the tasks.
 bbtc_status count_reset(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                         bool per_graph, cudaStream_t s);
 bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t nitems,
                          unsigned long long *vertex_count, bool per_graph, uint32_t timeout_ms,
-                         cudaStream_t s);
+                         cudaStream_t s, unsigned long long *task_cycles = nullptr);
 bbtc_status count_finish(const Plan &pl, cudaStream_t s);
 
 // a11: count with the blocks streamed from pinned host memory through a
@@ -162,7 +163,8 @@ struct StreamStats {
 };
 bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
                                unsigned long long *vertex_count, bool per_graph,
-                               uint32_t timeout_ms, cudaStream_t s, StreamStats *stats);
+                               uint32_t timeout_ms, cudaStream_t s, StreamStats *stats,
+                               unsigned long long *task_cycles = nullptr);
 
 // Work figures of the oriented graph (device): sum_{(u,v)} d+(v) and
 // sum_u d+(u)(d+(u)-1)/2.

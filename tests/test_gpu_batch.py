@@ -161,3 +161,21 @@ def test_timeout_is_reported_and_the_handle_stays_usable():
             g.count(p=1, timeout_ms=1, chunk=64)
         assert e.value.status == 4
         assert g.count(p=1) == full
+
+
+def test_per_task_cycles_and_estimator_study():
+    from paper_2009_12457_gb300 import workload
+    n, rp, ci = graphgen.rmat(14, 16, 1)
+    with bb.Graph(n, rp, ci) as g:
+        ref = g.count(p=4, per_task=True)
+        out = g.count(p=4, per_task=True, per_task_cycles=True)
+        assert np.array_equal(out["per_task"], ref["per_task"])  # measuring changes no count
+        cyc = out["per_task_cycles"]
+        plan = g.plan(4)
+        nnz = plan["block_nnz"]
+        tl = plan["tasks"]
+        has_work = np.array([nnz[i, j] > 0 and nnz[i, k] > 0 and nnz[j, k] > 0 for i, j, k in tl])
+        assert np.all(cyc[has_work] > 0) and np.all(cyc[~has_work] == 0)
+        s = workload.study(g, p=4, repeats=1)
+        assert set(s["coverage"]) == {"nnz", "density", "degree", "bbtc"}
+        assert all(0 < v <= 1.0 for c in s["coverage"].values() for v in c.values())

@@ -46,3 +46,39 @@ def test_autotuner_cache_round_trip(tmp_path):
     assert again.cache == json.loads(path.read_text())
     opts = autotune.Autotuner.opts(again.cache["m2^20_d2^5"])
     assert opts.p == 4 and opts.kernel == 2 and opts.chunk == 256
+
+
+def test_coverage_metric_by_hand():
+    from paper_2009_12457_gb300 import workload
+    # costs: task 3 is the heaviest, then 0, then 2, then 1
+    cost = np.array([5.0, 1.0, 2.0, 9.0])
+    perfect = np.array([5.0, 1.0, 2.0, 9.0])
+    assert workload.coverage(perfect, cost, xs=(1, 2, 3, 4)) == {1: 0.25, 2: 0.5, 3: 0.75, 4: 1.0}
+    # an estimate that ranks the heaviest task last needs the whole list for x = 1
+    bad = np.array([4.0, 3.0, 2.0, 1.0])
+    assert workload.coverage(bad, cost, xs=(1,))[1] == 1.0
+    # ties keep Alg. 4 order: all-equal estimates scan tasks 0,1,2,3
+    flat = np.zeros(4)
+    assert workload.coverage(flat, cost, xs=(1, 2))[1] == 1.0
+    assert workload.coverage(flat, cost, xs=(1, 2))[2] == 1.0
+
+
+def test_spearman_by_hand():
+    from paper_2009_12457_gb300 import workload
+    assert workload.spearman(np.array([1, 2, 3, 4]), np.array([10, 20, 30, 40])) == 1.0
+    assert workload.spearman(np.array([1, 2, 3, 4]), np.array([4, 3, 2, 1])) == -1.0
+    # ties take average ranks: x = [1, 1, 2], y = [1, 2, 3] -> ranks (0.5, 0.5, 2) vs (0, 1, 2)
+    r = workload.spearman(np.array([1, 1, 2]), np.array([1, 2, 3]))
+    assert abs(r - 0.8660254037844386) < 1e-12
+
+
+def test_estimates_from_a_plan():
+    from paper_2009_12457_gb300 import workload
+    plan = {"cuts": np.array([0, 2, 5]), "block_nnz": np.array([[3, 4], [0, 6]]),
+            "tasks": np.array([[0, 0, 0], [0, 0, 1], [0, 1, 1], [1, 1, 1]]),
+            "exec_time": np.array([4.5, 6.0, 8.0, 12.0])}
+    e = workload.estimates(plan)
+    assert np.allclose(e["nnz"], [9, 3 + 4 + 4, 4 + 6 + 4, 18])
+    assert np.allclose(e["degree"], [4.5, 1.5 + 2 + 2, 2 + 2 + 2, 6])
+    assert np.allclose(e["density"], [3 * 0.75, 0.75 + 4 / 6 + 4 / 6, 4 / 6 + 6 / 9 + 4 / 6, 3 * 6 / 9])
+    assert np.allclose(e["bbtc"], [4.5, 6.0, 8.0, 12.0])
