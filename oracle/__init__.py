@@ -86,6 +86,7 @@ def _declare(lib):
     lib.orc_tc_hmap.argtypes = [i64, P, P]
     lib.orc_tc_hmap.restype = u64
     lib.orc_per_vertex.argtypes = [i64, P, P, P, P]
+    lib.orc_edge_support.argtypes = [i64, P, P, P]
     lib.orc_cuts.argtypes = [i64, P, i32, P]
     lib.orc_block_nnz.argtypes = [i64, P, P, i32, P, P]
     lib.orc_num_tasks.argtypes = [i32]
@@ -173,6 +174,15 @@ def per_vertex(n: int, rp, ci, perm) -> np.ndarray:
     out = np.empty(max(n, 1), dtype=np.uint64)
     _load().orc_per_vertex(n, _p(rp), _p(ci), _p(perm), _p(out))
     return out[:n]
+
+
+def edge_support(n: int, rp, ci) -> np.ndarray:
+    """Triangles containing each oriented edge, by oriented-CSR position."""
+    rp = _c(rp, np.int64)
+    ci = _c(ci, np.int32)
+    out = np.zeros(max(int(rp[n]), 1), dtype=np.uint32)
+    _load().orc_edge_support(n, _p(rp), _p(ci), _p(out))
+    return out[:int(rp[n])]
 
 
 def cuts(n: int, rp, p: int) -> np.ndarray:

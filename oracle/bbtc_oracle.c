@@ -19,6 +19,7 @@
  *   task estimate + order      (Sec. 5, ExecTime)
  *   per-task count             (Sec. 4.3, Alg. 5 bbTC-Intersect, Alg. 6 bbTC-HMap)
  *   whole-graph count          (Sec. 3, Alg. 2 TC-Intersect with Alg. 1, Alg. 3 TC-HMap)
+ *   per-vertex and per-edge    (Alg. 9's per-vertex counts; edge support for k-truss, Sec. 1)
  *
  * Readings of the paper taken here (each is also listed in the design notes):
  *  - Alg. 1 compares A[b] = B[b] in its first branch; the intended test is
@@ -196,6 +197,30 @@ void orc_per_vertex(int64_t n, const int64_t *rp, const int32_t *ci, const int32
       while (a < rp[u + 1] && b < rp[v + 1]) {
         if (ci[a] == ci[b]) {
           cnt_out[perm[u]] += 1; cnt_out[perm[v]] += 1; cnt_out[perm[ci[a]]] += 1;
+          ++a; ++b;
+        } else if (ci[a] < ci[b]) ++a;
+        else ++b;
+      }
+    }
+}
+
+/*
+ * Edge support: for every oriented edge (u,v) at position e of the oriented
+ * CSR, the number of triangles that contain it. The paper names k-truss
+ * decomposition among the consumers of triangle counts (Sec. 1); an edge's
+ * support is its input. Each triangle u < v < w found by merging N(u) and
+ * N(v) adds one to (u,v), to (u,w) and to (v,w); the merge visits w at its
+ * position in both rows, so all three positions are known.
+ */
+void orc_edge_support(int64_t n, const int64_t *rp, const int32_t *ci, uint32_t *sup_out) {
+  memset(sup_out, 0, sizeof(uint32_t) * (size_t)(rp[n] > 0 ? rp[n] : 1));
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+      int64_t v = ci[e];
+      int64_t a = rp[u], b = rp[v];
+      while (a < rp[u + 1] && b < rp[v + 1]) {
+        if (ci[a] == ci[b]) {
+          sup_out[e] += 1; sup_out[a] += 1; sup_out[b] += 1;
           ++a; ++b;
         } else if (ci[a] < ci[b]) ++a;
         else ++b;

@@ -158,6 +158,13 @@ def pin_battery() -> list[str]:
         check(oracle.tc_hmap(n, pr["rowptr"], pr["colidx"]) == T, f"Alg.3 trial {trial}")
         pv = oracle.per_vertex(n, pr["rowptr"], pr["colidx"], pr["perm"])
         check(np.array_equal(pv, G.per_vertex_dense(*g)), f"per-vertex trial {trial}")
+        # edge support: common neighbours of each edge's endpoints (dense A @ A)
+        A2 = G.dense_adjacency(*g)
+        common = A2 @ A2
+        sup = oracle.edge_support(n, pr["rowptr"], pr["colidx"])
+        src = np.repeat(np.arange(n), np.diff(pr["rowptr"]))
+        a, b = pr["perm"][src], pr["perm"][pr["colidx"]]
+        check(np.array_equal(sup.astype(np.int64), common[a, b]), f"edge support trial {trial}")
         # the order: degree non-decreasing along positions, ties by id, edges upward
         A, deg, rank, perm, outdeg = positions_by_definition(*g)
         check(np.array_equal(pr["perm"], perm), f"degree order trial {trial}")

@@ -35,6 +35,10 @@ MUTANTS = {
                                "if (H[ci[f] - cuts[k]] == u && ci[f] != cuts[k]) ++tau;"),
     "per_vertex_wrong_corner": ("cnt_out[perm[u]] += 1; cnt_out[perm[v]] += 1;",
                                 "cnt_out[perm[u]] += 1; cnt_out[perm[u]] += 1;"),
+    "edge_support_drops_vw": ("sup_out[e] += 1; sup_out[a] += 1; sup_out[b] += 1;",
+                              "sup_out[e] += 1; sup_out[a] += 1; sup_out[a] += 1;"),
+    "edge_support_wrong_edge": ("sup_out[e] += 1; sup_out[a] += 1; sup_out[b] += 1;",
+                                "sup_out[e] += 1; sup_out[a] += 1; sup_out[b - 1 >= rp[v] ? b - 1 : b] += 1;"),
     "exec_time_min_not_max": ("(dik > djk ? dik : djk)", "(dik < djk ? dik : djk)"),
     "task_order_ascending": ("g_sort_est[a] > g_sort_est[b] ? -1 : 1",
                              "g_sort_est[a] < g_sort_est[b] ? -1 : 1"),

@@ -177,3 +177,51 @@ def test_vertex_triangles_sampled():
     for k in range(3, 9):
         for x in range(k):
             assert oracle.vertex_triangles(*G.complete(k), x) == G.choose(k - 1, 2)
+
+
+def _support_by_pair(g):
+    """Oracle edge support keyed by the original endpoint pair (min, max)."""
+    n = g[0]
+    pr = oracle.prepare(*g)
+    rp, ci, perm = pr["rowptr"], pr["colidx"], pr["perm"]
+    sup = oracle.edge_support(n, rp, ci)
+    out = {}
+    for r in range(n):
+        for e in range(int(rp[r]), int(rp[r + 1])):
+            a, b = int(perm[r]), int(perm[ci[e]])
+            out[(min(a, b), max(a, b))] = int(sup[e])
+    return out, pr
+
+
+def test_edge_support_closed_forms():
+    for k in range(3, 10):
+        sup, _ = _support_by_pair(G.complete(k))
+        assert len(sup) == G.choose(k, 2) and set(sup.values()) == {k - 2}
+    for k in range(4, 10):
+        sup, _ = _support_by_pair(G.wheel(k))
+        assert all(s == (2 if a == 0 else 1) for (a, b), s in sup.items())
+    sup, _ = _support_by_pair(G.friendship(5))
+    assert set(sup.values()) == {1}
+    sizes = (2, 3, 4)
+    part = np.repeat(np.arange(3), sizes)
+    sup, _ = _support_by_pair(G.complete_multipartite(sizes))
+    for (a, b), s in sup.items():
+        third = 3 - part[a] - part[b]
+        assert s == sizes[third]
+    sup, _ = _support_by_pair(G.grid(4, 5))
+    assert set(sup.values()) == {0}
+
+
+def test_edge_support_brute_force():
+    rng = np.random.default_rng(31)
+    for _ in range(40):
+        n = int(rng.integers(2, 30))
+        g = pins.with_noise(*G.gnp(n, float(rng.uniform(0.1, 0.9)), rng), rng)
+        A = G.dense_adjacency(*g)
+        common = A @ A
+        sup, pr = _support_by_pair(g)
+        assert len(sup) == int(A.sum()) // 2
+        for (a, b), s in sup.items():
+            assert A[a, b] == 1 and s == common[a, b]
+        T = oracle.tc_intersect(n, pr["rowptr"], pr["colidx"])
+        assert sum(sup.values()) == 3 * T
