@@ -418,7 +418,8 @@ def run_serve(args, world, rank, local_rank):
         bad = [r for r in reqs if r.status != 0]
         summ = serve.latency_summary(reqs)
         summ.update({"rate_hz": lam, "failed": len(bad), "cache_hits": srv.hits,
-                     "cache_misses": srv.misses, "evictions": srv.evictions})
+                     "cache_misses": srv.misses, "evictions": srv.evictions,
+                     "errors": srv.errors[:4]})
         results.append(summ)
     line = {
         "metric": METRIC, "impl": "serve", "unit": "graphs/s",

@@ -49,9 +49,12 @@ typedef enum {
 
 /* Per-task counting kernel (Sec. 4.3; the paper's isDense choice, Alg. 7). */
 typedef enum {
-  BBTC_KERNEL_AUTO = 0,      /* choose per task from the block densities */
+  BBTC_KERNEL_AUTO = 0,      /* choose per staged list N(G_jk, v): bitmap when its value
+                                range fits on chip, else hash table or sorted search by
+                                its length (hash_threshold) */
   BBTC_KERNEL_INTERSECT = 1, /* bbTC-Intersect (Alg. 5): sorted-list search */
-  BBTC_KERNEL_HASHMAP = 2    /* bbTC-HMap (Alg. 6): hash-table lookup */
+  BBTC_KERNEL_HASHMAP = 2    /* bbTC-HMap (Alg. 6): direct-address bitmap over the list's
+                                value range when it fits on chip, else hash table */
 } bbtc_kernel;
 
 /* bbtc_graph_create flags */
@@ -72,8 +75,10 @@ typedef struct {
   uint64_t *per_task_out;       /* NULL, or bbtc_num_tasks(p) uint64 in Alg. 4 order */
   void *stream;                 /* cudaStream_t to run on; NULL = the handle's own stream */
   uint32_t flags;               /* BBTC_OUT_DEVICE: the two output arrays are device pointers */
-  int32_t hash_threshold;       /* AUTO: tasks whose mean staged list exceeds this use HMap;
-                                   0 = built-in default */
+  int32_t hash_threshold;       /* AUTO: a staged list N(G_jk, v) whose value range is too
+                                   wide for a bitmap is hashed when it is longer than this,
+                                   else searched sorted; 0 = built-in default (16);
+                                   at most 2^28 */
   uint64_t *per_graph_out;      /* NULL, or one uint64 per graph of a batch handle
                                    (bbtc_graph_create_batch / bbtc_count_batch) */
   int32_t chunk;                /* in-edges per work item of the counting kernel; 0 = auto */
@@ -82,6 +87,10 @@ typedef struct {
                                     clock cycles the counting kernel's warps spent on each
                                     task's work items (the measured side of the Sec. 5
                                     workload estimate) */
+  uint32_t *per_edge_out;       /* NULL, or m uint32: the support of each oriented edge (the
+                                   triangles that contain it; the input of k-truss, Sec. 1),
+                                   in the order of bbtc_graph_get_oriented's colidx. Resident
+                                   counts only (device_budget_bytes = 0) */
 } bbtc_opts;
 
 #define BBTC_OUT_DEVICE 0x1u
@@ -158,15 +167,39 @@ bbtc_status bbtc_graph_create_batch(int32_t ng, const int64_t *vertex_offsets,
 bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts, uint64_t *count);
 
 /*
- * Count ng independent handles in one persistent launch: their oriented
- * CSRs are gathered on the device into one union (positions offset per
- * handle), planned once and counted by one kernel launch whose hits are
- * attributed to their graph. counts receives ng uint64 totals; per_graph
- * (nullable) receives each graph's status. Options other than p, kernel,
- * hash_threshold, chunk and stream are ignored (no per-task, per-vertex or
- * per-graph outputs). p = 0 picks p from the union's size.
- * Errors: EINVAL for ng < 0 or a NULL handle (its status is EINVAL and the
- * others are still counted); ENOMEM; ECUDA.
+ * Build the resident plan of the handle for opts' p (0 = automatic), kernel,
+ * hash_threshold and chunk -- partition, blocks, tasks, estimates and work
+ * items (Sec. 2, Sec. 4.1-4.2, Sec. 5) -- without counting; keep it when it
+ * already matches. Later counts with the same options only read the plan.
+ * Other options are ignored. Synchronous.
+ * Errors: EINVAL (NULL handle, bad options); ENOMEM; ECUDA.
+ */
+bbtc_status bbtc_graph_plan(bbtc_graph_t g, const bbtc_opts *opts);
+
+/*
+ * Count ng independent handles in one persistent launch (Sec. 4.2 tasks of
+ * all of them drained together).
+ *
+ * Resident (device_budget_bytes = 0): each handle keeps its own plan for
+ * (p, kernel, hash_threshold, chunk) -- built first, on the handle, when it
+ * does not match -- and one counting launch takes the work items of all the
+ * handles, largest handles first. p = 0 picks p per handle from its size.
+ * Handles that already hold a matching resident plan are only read, so
+ * concurrent calls on other streams may share them.
+ * Under a device budget: the handles' oriented CSRs are gathered into one
+ * union (positions offset per handle), planned once and counted with its
+ * blocks streamed; p = 0 picks p from the union's size.
+ *
+ *   gs         ng handles (NULL entries are reported, the rest still counted)
+ *   counts     receives ng uint64 totals (host)
+ *   per_graph  NULL, or receives each handle's status
+ *
+ * Options other than p, kernel, hash_threshold, chunk, timeout_ms, stream and
+ * device_budget_bytes are ignored (no per-task, per-vertex or per-graph
+ * outputs).
+ * Errors: EINVAL for ng < 0, a NULL handle (its status is EINVAL and the
+ * others are still counted) or handles on different devices; ENOMEM;
+ * ETIMEOUT; ECUDA.
  */
 bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts *opts,
                              uint64_t *counts, bbtc_status *per_graph);

@@ -20,7 +20,7 @@ from . import _build
 
 __all__ = [
     "BbtcError", "Graph", "bbtc_graph_create", "bbtc_graph_create_async", "bbtc_count",
-    "bbtc_count_batch", "bbtc_graph_destroy", "bbtc_last_error", "bbtc_num_tasks",
+    "bbtc_count_batch", "bbtc_graph_plan", "bbtc_graph_destroy", "bbtc_last_error", "bbtc_num_tasks",
     "bbtc_opts_init", "bbtc_graph_get_info", "bbtc_graph_get_oriented", "bbtc_graph_get_plan",
     "bbtc_graph_get_timings", "bbtc_kernel_launches", "bbtc_count_noalloc",
     "bbtc_graph_create_batch", "bbtc_count_async", "BatchGraph",
@@ -58,6 +58,7 @@ class bbtc_opts(ctypes.Structure):
         ("chunk", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
         ("per_task_cycles_out", ctypes.c_void_p),
+        ("per_edge_out", ctypes.c_void_p),
     ]
 
 
@@ -115,6 +116,8 @@ def load():
         lib.bbtc_count.restype = st
         lib.bbtc_count_batch.argtypes = [P, i32, ctypes.POINTER(bbtc_opts), P, P]
         lib.bbtc_count_batch.restype = st
+        lib.bbtc_graph_plan.argtypes = [P, ctypes.POINTER(bbtc_opts)]
+        lib.bbtc_graph_plan.restype = st
         lib.bbtc_graph_destroy.argtypes = [P]
         lib.bbtc_graph_destroy.restype = None
         lib.bbtc_last_error.argtypes = []
@@ -212,7 +215,7 @@ def bbtc_graph_destroy(handle: int) -> None:
 def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
               device_budget_bytes: int = 0, per_vertex_out=None, per_task_out=None,
               stream=None, hash_threshold: int = 0, per_graph_out=None,
-              chunk: int = 0, per_task_cycles_out=None) -> bbtc_opts:
+              chunk: int = 0, per_task_cycles_out=None, per_edge_out=None) -> bbtc_opts:
     o = bbtc_opts_init()
     o.p = p
     o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
@@ -221,7 +224,8 @@ def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
     o.hash_threshold = hash_threshold
     o.chunk = chunk
     outs = [(_ptr(a), a is not None)
-            for a in (per_vertex_out, per_task_out, per_graph_out, per_task_cycles_out)]
+            for a in (per_vertex_out, per_task_out, per_graph_out, per_task_cycles_out,
+                      per_edge_out)]
     kinds = {dev for (addr, dev), given in outs if given}
     if len(kinds) > 1:
         raise ValueError("optional outputs must all be host arrays or all device arrays")
@@ -229,6 +233,7 @@ def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
     o.per_task_out = outs[1][0][0] or None
     o.per_graph_out = outs[2][0][0] or None
     o.per_task_cycles_out = outs[3][0][0] or None
+    o.per_edge_out = outs[4][0][0] or None
     o.flags = OUT_DEVICE if kinds == {True} else 0
     o.stream = _stream_ptr(stream) or None
     return o
@@ -270,6 +275,11 @@ def bbtc_count_noalloc(handle: int, p: int, count_dev, per_task_dev=None, stream
     if not c_dev or (per_task_dev is not None and not t_dev):
         raise ValueError("bbtc_count_noalloc writes device buffers only")
     _check(load().bbtc_count_noalloc(handle, p, c, t or None, _stream_ptr(stream) or None))
+
+
+def bbtc_graph_plan(handle: int, opts: bbtc_opts | None = None) -> None:
+    """Build (or keep) the handle's resident plan for the options, without counting."""
+    _check(load().bbtc_graph_plan(handle, ctypes.byref(opts) if opts is not None else None))
 
 
 def bbtc_count_batch(handles, opts: bbtc_opts | None = None):
@@ -339,9 +349,10 @@ class Graph:
     def count(self, p: int = 0, kernel: str = "auto", per_vertex: bool = False,
               per_task: bool = False, timeout_ms: int = 0, device_budget_bytes: int = 0,
               stream=None, hash_threshold: int = 0, per_graph: bool = False, chunk: int = 0,
-              per_task_cycles: bool = False):
+              per_task_cycles: bool = False, per_edge: bool = False):
         """Total triangle count, or a dict with per-task / per-vertex / per-graph counts
-        (and, with per_task_cycles, the SM cycles spent on each task)."""
+        (with per_task_cycles, the SM cycles spent on each task; with per_edge, the
+        support of each oriented edge in the order of get_oriented()'s colidx)."""
         pt = np.zeros(max(bbtc_num_tasks(p), 1), dtype=np.uint64) if per_task and p > 0 else None
         if per_task and p == 0:
             raise ValueError("per_task needs an explicit p")
@@ -351,10 +362,12 @@ class Graph:
         if per_task_cycles and p == 0:
             raise ValueError("per_task_cycles needs an explicit p")
         cyc = np.zeros(max(bbtc_num_tasks(p), 1), dtype=np.uint64) if per_task_cycles else None
+        m = self.info()["m"] if per_edge else 0
+        pe = np.zeros(max(m, 1), dtype=np.uint32) if per_edge else None
         opts = make_opts(p, kernel, timeout_ms, device_budget_bytes, pv, pt, stream,
-                         hash_threshold, pg, chunk, cyc)
+                         hash_threshold, pg, chunk, cyc, pe)
         total = bbtc_count(self.handle, opts)
-        if not per_task and not per_vertex and not per_graph and not per_task_cycles:
+        if not (per_task or per_vertex or per_graph or per_task_cycles or per_edge):
             return total
         out = {"total": total}
         if per_task:
@@ -365,10 +378,20 @@ class Graph:
             out["per_graph"] = pg[:ng]
         if per_task_cycles:
             out["per_task_cycles"] = cyc[:bbtc_num_tasks(p)]
+        if per_edge:
+            out["per_edge"] = pe[:m]
         return out
 
     def info(self) -> dict:
         return bbtc_graph_get_info(self.handle)
+
+    def edge_support(self, p: int = 0, kernel: str = "auto"):
+        """Support of every edge (the number of triangles containing it, the input of
+        k-truss): arrays (u, v, support) with u, v original vertex ids."""
+        sup = self.count(p=p, kernel=kernel, per_edge=True)["per_edge"]
+        o = self.oriented()
+        src = np.repeat(np.arange(len(o["perm"]), dtype=np.int64), np.diff(o["rowptr"]))
+        return o["perm"][src], o["perm"][o["colidx"]], sup
 
     def oriented(self) -> dict:
         return bbtc_graph_get_oriented(self.handle)

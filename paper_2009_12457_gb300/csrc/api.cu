@@ -128,8 +128,8 @@ bbtc_status check_opts(const bbtc_opts *opts, bbtc_opts *out) {
     set_error("kernel = %d is not a bbtc_kernel", out->kernel);
     return BBTC_EINVAL;
   }
-  if (out->hash_threshold < 0) {
-    set_error("hash_threshold = %d is negative", out->hash_threshold);
+  if (out->hash_threshold < 0 || out->hash_threshold > (1 << 28)) {
+    set_error("hash_threshold = %d is outside 0..2^28", out->hash_threshold);
     return BBTC_EINVAL;
   }
   if (out->hash_threshold == 0) out->hash_threshold = 16;
@@ -352,6 +352,10 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   const int p = opts.p == 0 ? default_p(g) : opts.p;
   cudaStream_t s = opts.stream ? (cudaStream_t)opts.stream : g->stream;
   const bool budgeted = opts.device_budget_bytes != 0;
+  if (budgeted && opts.per_edge_out) {
+    set_error("bbtc_count: per_edge_out needs a resident count (device_budget_bytes = 0)");
+    return BBTC_EINVAL;
+  }
   // a resident count needs the block arrays on the device: a plan that was
   // streamed (its arrays now in host memory) is rebuilt
   if (!budgeted && g->plan.streamed) free_plan(&g->plan, s);
@@ -369,6 +373,11 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
     BBTC_TRY(scratch.get(&task_cycles, pl.ntasks));
     BBTC_CUDA(cudaMemsetAsync(task_cycles, 0, sizeof(uint64_t) * (size_t)pl.ntasks, s));
   }
+  unsigned *edge_sup = nullptr;
+  if (opts.per_edge_out) {
+    BBTC_TRY(scratch.get(&edge_sup, g->m > 0 ? g->m : 1));
+    BBTC_CUDA(cudaMemsetAsync(edge_sup, 0, sizeof(unsigned) * (size_t)(g->m > 0 ? g->m : 1), s));
+  }
   const bool per_graph = opts.per_graph_out != nullptr;
   if (budgeted) {
     StreamStats st;
@@ -380,7 +389,7 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
     g->stream_stats_total_ms = st.total_ms;
   } else {
     BBTC_TRY(run_count(g, pl, vertex_count, per_graph, opts.timeout_ms, s, g->ev[4], g->ev[5],
-                       task_cycles));
+                       task_cycles, edge_sup));
     g->stream_stats_total_ms = -1.0;
   }
   unsigned long long head[SCR_TASKS] = {0, 0, 0};
@@ -401,6 +410,13 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   if (task_cycles)
     BBTC_CUDA(cudaMemcpyAsync(opts.per_task_cycles_out, task_cycles,
                               sizeof(uint64_t) * (size_t)pl.ntasks, kind, s));
+  if (edge_sup && g->m > 0) {
+    unsigned *by_csr = nullptr;
+    BBTC_TRY(scratch.get(&by_csr, g->m));
+    BBTC_TRY(edge_support_to_csr(g, pl, edge_sup, by_csr, s));
+    BBTC_CUDA(cudaMemcpyAsync(opts.per_edge_out, by_csr, sizeof(uint32_t) * (size_t)g->m, kind,
+                              s));
+  }
   if (opts.per_vertex_out && g->n > 0) {
     unsigned long long *by_id = nullptr;
     BBTC_TRY(scratch.get(&by_id, g->n));
@@ -430,10 +446,10 @@ bbtc_status bbtc_count_async(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t 
               "with bbtc_count (without a device budget) or bbtc_graph_get_plan first");
     return BBTC_EINVAL;
   }
-  if (opts.per_vertex_out || opts.per_task_cycles_out ||
+  if (opts.per_vertex_out || opts.per_task_cycles_out || opts.per_edge_out ||
       ((opts.per_task_out || opts.per_graph_out) && !(opts.flags & BBTC_OUT_DEVICE))) {
     set_error("bbtc_count_async: outputs must be device pointers (BBTC_OUT_DEVICE) and "
-              "per_vertex_out / per_task_cycles_out must be NULL");
+              "per_vertex_out / per_task_cycles_out / per_edge_out must be NULL");
     return BBTC_EINVAL;
   }
   DeviceGuard dg(g->device);
@@ -449,6 +465,23 @@ bbtc_status bbtc_count_async(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t 
   if (per_graph)
     BBTC_CUDA(cudaMemcpyAsync(opts.per_graph_out, pl.scratch + SCR_TASKS + pl.ntasks,
                               sizeof(uint64_t) * (size_t)g->ng, cudaMemcpyDeviceToDevice, s));
+  return BBTC_OK;
+}
+
+bbtc_status bbtc_graph_plan(bbtc_graph_t g, const bbtc_opts *opts_in) {
+  clear_error();
+  if (!g) {
+    set_error("bbtc_graph_plan: NULL handle");
+    return BBTC_EINVAL;
+  }
+  bbtc_opts opts;
+  BBTC_TRY(check_opts(opts_in, &opts));
+  DeviceGuard dg(g->device);
+  const int p = opts.p == 0 ? default_p(g) : opts.p;
+  cudaStream_t s = opts.stream ? (cudaStream_t)opts.stream : g->stream;
+  if (g->plan.streamed) free_plan(&g->plan, s);
+  BBTC_TRY(build_plan(g, p, opts.kernel, opts.hash_threshold, opts.chunk, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
   return BBTC_OK;
 }
 
@@ -487,7 +520,33 @@ bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts
     }
   }
   bbtc_status st = BBTC_OK;
-  if (nv > 0) {
+  for (int32_t x = 1; x < nv && st == BBTC_OK; ++x)
+    if (valid[x]->device != valid[0]->device) {
+      set_error("bbtc_count_batch: handles %d and %d live on different devices", where[0],
+                where[x]);
+      st = BBTC_EINVAL;
+    }
+  if (nv > 0 && st == BBTC_OK && o.device_budget_bytes == 0) {
+    // resident: every handle keeps (or first builds) its own plan, and one
+    // launch drains the work items of all of them
+    DeviceGuard dg(valid[0]->device);
+    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : valid[0]->stream;
+    for (int32_t x = 0; x < nv && st == BBTC_OK; ++x) {
+      bbtc_graph *h = valid[x];
+      const int p = o.p == 0 ? default_p(h) : o.p;
+      if (h->plan.streamed) free_plan(&h->plan, s);
+      st = build_plan(h, p, o.kernel, o.hash_threshold, o.chunk, s);
+    }
+    uint64_t *sub = st == BBTC_OK ? new (std::nothrow) uint64_t[(size_t)nv] : nullptr;
+    if (st == BBTC_OK && !sub) st = BBTC_ENOMEM;
+    if (st == BBTC_OK) st = count_plans(valid, nv, o.timeout_ms, s, sub);
+    if (st == BBTC_OK)
+      for (int32_t x = 0; x < nv; ++x) counts[where[x]] = sub[x];
+    if (st != BBTC_OK && per_graph)
+      for (int32_t x = 0; x < nv; ++x) per_graph[where[x]] = st;
+    delete[] sub;
+  } else if (nv > 0 && st == BBTC_OK) {
+    // under a device budget: count the union of the handles, streamed
     DeviceGuard dg(valid[0]->device);
     cudaStream_t s = o.stream ? (cudaStream_t)o.stream : valid[0]->stream;
     bbtc_graph *u = nullptr;
@@ -499,6 +558,7 @@ bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts
       uo.per_task_out = nullptr;
       uo.per_vertex_out = nullptr;
       uo.per_task_cycles_out = nullptr;
+      uo.per_edge_out = nullptr;
       uo.per_graph_out = sub;
       uo.flags = 0;
       uo.stream = s;

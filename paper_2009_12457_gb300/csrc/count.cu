@@ -11,6 +11,9 @@
 //
 // Work: a persistent grid; each warp takes work items (task, in-edge range)
 // from a global counter, heaviest task first, until none remain.
+#include <algorithm>
+#include <vector>
+
 #include "graph.cuh"
 #include "primitives.cuh"
 
@@ -31,11 +34,12 @@ struct CountParams {
   const int32_t *gid;               // graph of each position (MODE & 2)
   unsigned long long *graph_count;  // per-graph counts (MODE & 2)
   unsigned long long *task_cycles;  // nullable: SM cycles spent on each task's items
+  unsigned *edge_sup;               // per-edge support by position in the block columns (MODE & 4)
   int32_t *status;
   uint64_t timeout_ns;
 };
 
-constexpr int MODE_VERTEX = 1, MODE_GRAPH = 2;
+constexpr int MODE_VERTEX = 1, MODE_GRAPH = 2, MODE_EDGE = 4;
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -46,6 +50,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Per-warp shared staging area for N(G_jk, v) (int32 slots).
 constexpr int STAGE = 2048;
 constexpr int MIN_STAGE = 8;
+constexpr int ST_NONE = 0, ST_SORTED = 1, ST_HASH = 2, ST_BITMAP = 3;
 constexpr int32_t EMPTY = -1;
 
 __device__ __forceinline__ uint32_t hash_slot(int32_t w, int log2h) {
@@ -95,6 +100,7 @@ template <int MODE>
 __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
   constexpr bool PER_VERTEX = (MODE & MODE_VERTEX) != 0;
   constexpr bool PER_GRAPH = (MODE & MODE_GRAPH) != 0;
+  constexpr bool PER_EDGE = (MODE & MODE_EDGE) != 0;
   extern __shared__ __align__(16) unsigned char count_smem_raw[];
   const unsigned lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
@@ -104,8 +110,8 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
   const uint64_t t_start = P.timeout_ns ? global_ns() : 0;
   // (task, v) whose N(G_jk, v) is in `stage`, and how it is stored
   unsigned long long staged_tag = ~0ull;
-  int staged_len = 0, staged_log2h = 0;
-  bool staged_hash = false;
+  int staged_len = 0, staged_log2h = 0, staged_mode = ST_NONE;
+  int32_t staged_first = 0;
 
   for (;;) {
     unsigned long long it = 0;
@@ -119,7 +125,8 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
     const WorkItem w = P.items[it];
     const int t = w.task;
     const long long t_item = P.task_cycles ? clock64() : 0;
-    const bool use_hash = (w.flags & 1) != 0;
+    const int kflag = w.flags & 3;  // 0 INTERSECT, 1 HASHMAP, 2 AUTO (per list)
+    const int hash_min = w.flags >> 2;  // AUTO: longer lists hash, shorter ones sorted
     const TaskDesc &d = P.desc[t];
     // block arrays are indexed locally: in-edge x at [x - ie_off], column
     // position q at [q - ci_*_off] (the offsets are 0 when the plan is resident)
@@ -138,6 +145,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
 
     int64_t base = w.x0;
     while (base < w.x1) {
+      const int64_t batch_x0 = base;  // in-edge of lane 0; lane l's is batch_x0 + l
       const int64_t x = base + lane;
       const bool valid = x < w.x1;
       const int32_t v = valid ? ie_v[x - ie_off] : -1;
@@ -192,45 +200,82 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
       if (total == 0) continue;
 
-      // stage N(G_jk, v) once per (task, v): sorted copy (bbTC-Intersect) or
-      // hash table (bbTC-HMap)
+      // stage N(G_jk, v) once per (task, v) in one of three forms:
+      //  - bitmap over [first, last] of the list (Alg. 6's direct-address
+      //    table H, windowed to the list's value range) when that range has at
+      //    most STAGE * 32 values;
+      //  - open-addressed hash table (at most half full) otherwise;
+      //  - sorted copy (bbTC-Intersect, Alg. 5), searched by halving.
+      // The item's kernel flag picks sorted (INTERSECT), bitmap-else-hash
+      // (HASHMAP), or, per list, bitmap, then hash for long lists, then sorted
+      // (AUTO).
       const int blen = (int)(b1 - b0);
       bool staged = false;
-      if (uniform && blen >= MIN_STAGE && blen <= STAGE) {
-        const bool want_hash = use_hash && blen <= STAGE / 2;
+      if (uniform && blen >= MIN_STAGE) {
         const unsigned long long tag =
-            ((unsigned long long)(uint32_t)t << 33) | ((unsigned long long)(uint32_t)v0 << 1) |
-            (want_hash ? 1ull : 0ull);
+            ((unsigned long long)(uint32_t)t << 33) | ((unsigned long long)(uint32_t)v0 << 2);
         if (tag == staged_tag) {
           staged = true;
         } else if (nb == 32 || total >= (uint32_t)blen / 2) {
-          __syncwarp();
-          if (want_hash) {
-            int log2h = 5;
-            while ((1 << log2h) < 2 * blen) ++log2h;
-            const int hsize = 1 << log2h;
-            for (int i = lane; i < hsize; i += 32) stage[i] = EMPTY;
-            __syncwarp();
-            const uint32_t hmask = (uint32_t)hsize - 1u;
-            for (int i = lane; i < blen; i += 32) {
-              const int32_t key = ci_jk[b0 + i];
-              // linear probing from the first slot of the key's 4-slot group,
-              // the order in which hash_contains reads the table
-              uint32_t h = hash_slot(key, log2h) & ~3u;
-              for (int n = 0; n < hsize; ++n) {
-                if (atomicCAS(&stage[h], EMPTY, key) == EMPTY) break;
-                h = (h + 1) & hmask;
-              }
-            }
-            staged_log2h = log2h;
-          } else {
-            for (int i = lane; i < blen; i += 32) stage[i] = ci_jk[b0 + i];
+          int32_t first = 0, last = 0;
+          if (lane == 0) {
+            first = ci_jk[b0];
+            last = ci_jk[b1 - 1];
           }
-          __syncwarp();
-          staged_tag = tag;
-          staged_len = blen;
-          staged_hash = want_hash;
-          staged = true;
+          first = __shfl_sync(0xffffffffu, first, 0);
+          last = __shfl_sync(0xffffffffu, last, 0);
+          const int64_t span = (int64_t)last - first + 1;
+          int mode = ST_NONE;
+          if (kflag == 0) {
+            if (blen <= STAGE) mode = ST_SORTED;
+          } else if (span <= (int64_t)STAGE * 32) {
+            mode = ST_BITMAP;
+          } else if (blen <= STAGE / 2 && (kflag == 1 || blen > hash_min)) {
+            mode = ST_HASH;
+          } else if (kflag == 2 && blen <= STAGE) {
+            mode = ST_SORTED;
+          }
+          if (mode != ST_NONE) {
+            __syncwarp();
+            if (mode == ST_BITMAP) {
+              const int words4 = (int)(((span + 31) >> 5) + 3) >> 2;
+              int4 *s4 = reinterpret_cast<int4 *>(stage);
+              for (int i = lane; i < words4; i += 32) s4[i] = make_int4(0, 0, 0, 0);
+              __syncwarp();
+              for (int i = lane; i < blen; i += 32) {
+                const uint32_t d = (uint32_t)(ci_jk[b0 + i] - first);
+                atomicOr(reinterpret_cast<unsigned *>(stage) + (d >> 5), 1u << (d & 31u));
+              }
+              staged_first = first;
+              staged_len = (int)span;
+            } else if (mode == ST_HASH) {
+              int log2h = 5;
+              while ((1 << log2h) < 2 * blen) ++log2h;
+              const int hsize = 1 << log2h;
+              for (int i = lane; i < hsize; i += 32) stage[i] = EMPTY;
+              __syncwarp();
+              const uint32_t hmask = (uint32_t)hsize - 1u;
+              for (int i = lane; i < blen; i += 32) {
+                const int32_t key = ci_jk[b0 + i];
+                // linear probing from the first slot of the key's 4-slot group,
+                // the order in which hash_contains reads the table
+                uint32_t h = hash_slot(key, log2h) & ~3u;
+                for (int n = 0; n < hsize; ++n) {
+                  if (atomicCAS(&stage[h], EMPTY, key) == EMPTY) break;
+                  h = (h + 1) & hmask;
+                }
+              }
+              staged_log2h = log2h;
+              staged_len = blen;
+            } else {
+              for (int i = lane; i < blen; i += 32) stage[i] = ci_jk[b0 + i];
+              staged_len = blen;
+            }
+            __syncwarp();
+            staged_tag = tag;
+            staged_mode = mode;
+            staged = true;
+          }
         }
       }
 
@@ -254,10 +299,11 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
       int64_t addr = rec.s0[0];  // ci_ik index of probe q is addr + q
       // U probes per lane per round: their loads are issued before any
       // lookup, so each lane keeps U global loads in flight
-      constexpr int U = 8;
+      constexpr int U = 4;
       for (uint32_t qb = lane; qb < total; qb += 32 * U) {
         int32_t wv[U];
         int own[U];
+        int64_t qpos[PER_EDGE ? U : 1];  // local column position of each probe
 #pragma unroll
         for (int r = 0; r < U; ++r) {
           const uint32_t q = qb + 32u * r;
@@ -271,6 +317,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
             }
             wv[r] = ci_ik[addr + q];
             own[r] = o;
+            if (PER_EDGE) qpos[r] = addr + q;
           }
         }
 #pragma unroll
@@ -278,8 +325,15 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
           if (own[r] < 0) continue;
           bool hit;
           if (staged) {
-            hit = staged_hash ? hash_contains(stage, staged_log2h, wv[r])
-                              : sorted_contains(stage, staged_len, wv[r]);
+            if (staged_mode == ST_BITMAP) {
+              const uint32_t d = (uint32_t)(wv[r] - staged_first);
+              hit = d < (uint32_t)staged_len &&
+                    ((reinterpret_cast<const unsigned *>(stage)[d >> 5] >> (d & 31u)) & 1u);
+            } else if (staged_mode == ST_HASH) {
+              hit = hash_contains(stage, staged_log2h, wv[r]);
+            } else {
+              hit = sorted_contains(stage, staged_len, wv[r]);
+            }
           } else {
             const int64_t lo = uniform ? b0 : rec.b0[own[r]];
             const int64_t hi = uniform ? b1 : rec.b1[own[r]];
@@ -292,6 +346,18 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
               atomicAdd(&P.vcount[rec.u[own[r]]], 1ull);
               atomicAdd(&P.vcount[rec.v[own[r]]], 1ull);
               atomicAdd(&P.vcount[wv[r]], 1ull);
+            }
+            if (PER_EDGE) {
+              // the triangle's three edges, by position in the block columns:
+              // (u,v) from the in-edge record, (u,w) from the probe, (v,w)
+              // found in N(G_jk, v)
+              const int o = own[r];
+              const int64_t lo = uniform ? b0 : rec.b0[o];
+              const int64_t hi = uniform ? b1 : rec.b1[o];
+              const int64_t pvw = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, wv[r]);
+              atomicAdd(&P.edge_sup[ie_e[batch_x0 + o - ie_off]], 1u);
+              atomicAdd(&P.edge_sup[qpos[r] + ik_off], 1u);
+              atomicAdd(&P.edge_sup[pvw + jk_off], 1u);
             }
             if (PER_GRAPH) {
               // every in-edge into v comes from v's own graph
@@ -367,6 +433,10 @@ bbtc_status configure_count_kernels(Plan *pl) {
   BBTC_TRY(configure_mode<1>(&pl->blocks_per_sm[1]));
   BBTC_TRY(configure_mode<2>(&pl->blocks_per_sm[2]));
   BBTC_TRY(configure_mode<3>(&pl->blocks_per_sm[3]));
+  BBTC_TRY(configure_mode<4>(&pl->blocks_per_sm[4]));
+  BBTC_TRY(configure_mode<5>(&pl->blocks_per_sm[5]));
+  BBTC_TRY(configure_mode<6>(&pl->blocks_per_sm[6]));
+  BBTC_TRY(configure_mode<7>(&pl->blocks_per_sm[7]));
   return BBTC_OK;
 }
 
@@ -403,7 +473,7 @@ bbtc_status count_reset(bbtc_graph *g, const Plan &pl, unsigned long long *verte
 
 bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t nitems,
                          unsigned long long *vertex_count, bool per_graph, uint32_t timeout_ms,
-                         cudaStream_t s, unsigned long long *task_cycles) {
+                         cudaStream_t s, unsigned long long *task_cycles, unsigned *edge_sup) {
   if (nitems <= 0) return BBTC_OK;
   unsigned long long *scr = pl.scratch;
   BBTC_CUDA(cudaMemsetAsync(scr + SCR_HEAD, 0, sizeof(unsigned long long), s));
@@ -419,7 +489,9 @@ bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t n
   P.status = reinterpret_cast<int32_t *>(scr + SCR_STATUS);
   P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
   P.task_cycles = task_cycles;
-  const int mode = (vertex_count ? MODE_VERTEX : 0) | (per_graph ? MODE_GRAPH : 0);
+  P.edge_sup = edge_sup;
+  const int mode = (vertex_count ? MODE_VERTEX : 0) | (per_graph ? MODE_GRAPH : 0) |
+                   (edge_sup ? MODE_EDGE : 0);
   int64_t blocks = (int64_t)num_sms() * pl.blocks_per_sm[mode];
   const int64_t need = (nitems + CT_NT / 32 - 1) / (CT_NT / 32);
   if (blocks > need) blocks = need;
@@ -428,7 +500,11 @@ bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t n
     case 0: k_count<0><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
     case 1: k_count<1><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
     case 2: k_count<2><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
-    default: k_count<3><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+    case 3: k_count<3><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+    case 4: k_count<4><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+    case 5: k_count<5><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+    case 6: k_count<6><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
+    default: k_count<7><<<(unsigned)blocks, CT_NT, smem, s>>>(P); break;
   }
   BBTC_LAUNCH_CHECK();
   return BBTC_OK;
@@ -444,13 +520,127 @@ bbtc_status count_finish(const Plan &pl, cudaStream_t s) {
 bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                       bool per_graph, uint32_t timeout_ms, cudaStream_t s,
                       cudaEvent_t ev_begin, cudaEvent_t ev_end,
-                      unsigned long long *task_cycles) {
+                      unsigned long long *task_cycles, unsigned *edge_sup) {
   BBTC_TRY(count_reset(g, pl, vertex_count, per_graph, s));
   if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
   BBTC_TRY(count_launch(g, pl, 0, pl.nitems, vertex_count, per_graph, timeout_ms, s,
-                        task_cycles));
+                        task_cycles, edge_sup));
   if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
   return count_finish(pl, s);
+}
+
+// --------------------------------------------- several plans, one launch
+//
+// A batch of resident handles is counted without copying them into a union:
+// each handle keeps its own plan, and one persistent launch drains the work
+// items of all of them. The descriptors of the handles' tasks are gathered
+// into one array (a task is found through its descriptor alone), and each
+// handle's items are copied with their task index moved to the handle's
+// first slot in that array.
+
+namespace {
+
+struct PlanRef {
+  const TaskDesc *desc;
+  const WorkItem *items;
+  int64_t ntasks, nitems;
+  int64_t task_base, item_base;
+};
+
+__global__ void k_gather_plans(const PlanRef *__restrict__ refs, int32_t nref,
+                               TaskDesc *__restrict__ desc, WorkItem *__restrict__ items) {
+  for (int32_t r = blockIdx.x; r < nref; r += gridDim.x) {
+    const PlanRef f = refs[r];
+    for (int64_t t = threadIdx.x; t < f.ntasks; t += blockDim.x) desc[f.task_base + t] = f.desc[t];
+    for (int64_t x = threadIdx.x; x < f.nitems; x += blockDim.x) {
+      WorkItem w = f.items[x];
+      w.task += (int32_t)f.task_base;
+      items[f.item_base + x] = w;
+    }
+  }
+}
+
+}  // namespace
+
+bbtc_status count_plans(bbtc_graph *const *gs, int32_t ng, uint32_t timeout_ms, cudaStream_t s,
+                        uint64_t *counts) {
+  // largest item lists first, so that small graphs fill the end of the launch
+  std::vector<int32_t> order((size_t)ng);
+  for (int32_t i = 0; i < ng; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return gs[a]->plan.nitems > gs[b]->plan.nitems;
+  });
+  std::vector<PlanRef> refs((size_t)ng);
+  std::vector<int64_t> task_base((size_t)ng);
+  int64_t ntasks = 0, nitems = 0;
+  int blocks_per_sm = 0;
+  for (int32_t r = 0; r < ng; ++r) {
+    const Plan &pl = gs[order[(size_t)r]]->plan;
+    if (pl.streamed || pl.p < 1) {
+      set_error("internal: count_plans needs resident plans");
+      return BBTC_EINTERNAL;
+    }
+    refs[(size_t)r] = PlanRef{pl.desc, pl.items, pl.ntasks, pl.nitems, ntasks, nitems};
+    task_base[(size_t)order[(size_t)r]] = ntasks;
+    ntasks += pl.ntasks;
+    nitems += pl.nitems;
+    if (pl.blocks_per_sm[0] > blocks_per_sm) blocks_per_sm = pl.blocks_per_sm[0];
+  }
+  if (ntasks > INT32_MAX) {
+    set_error("bbtc_count_batch: %lld tasks in one batch exceed the 32-bit task index",
+              (long long)ntasks);
+    return BBTC_EINVAL;
+  }
+  Scratch scratch(s);
+  PlanRef *d_refs = nullptr;
+  TaskDesc *desc = nullptr;
+  WorkItem *items = nullptr;
+  unsigned long long *counters = nullptr;  // [0] head, [1] status, [2, 2 + T) per task
+  BBTC_TRY(scratch.get(&d_refs, ng));
+  BBTC_TRY(scratch.get(&desc, ntasks));
+  BBTC_TRY(scratch.get(&items, nitems));
+  BBTC_TRY(scratch.get(&counters, 2 + ntasks));
+  BBTC_CUDA(cudaMemcpyAsync(d_refs, refs.data(), sizeof(PlanRef) * (size_t)ng,
+                            cudaMemcpyHostToDevice, s));
+  BBTC_CUDA(cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * (size_t)(2 + ntasks), s));
+  k_gather_plans<<<(unsigned)std::min<int64_t>(ng, 4096), 256, 0, s>>>(d_refs, ng, desc, items);
+  BBTC_LAUNCH_CHECK();
+  if (nitems > 0) {
+    CountParams P;
+    P.desc = desc;
+    P.items = items;
+    P.nitems = nitems;
+    P.head = counters;
+    P.task_count = counters + 2;
+    P.vcount = nullptr;
+    P.gid = nullptr;
+    P.graph_count = nullptr;
+    P.task_cycles = nullptr;
+    P.edge_sup = nullptr;
+    P.status = reinterpret_cast<int32_t *>(counters + 1);
+    P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
+    if (blocks_per_sm < 1) BBTC_TRY(configure_mode<0>(&blocks_per_sm));
+    int64_t blocks = (int64_t)num_sms() * blocks_per_sm;
+    const int64_t need = (nitems + CT_NT / 32 - 1) / (CT_NT / 32);
+    if (blocks > need) blocks = need;
+    k_count<0><<<(unsigned)blocks, CT_NT, count_smem_bytes(), s>>>(P);
+    BBTC_LAUNCH_CHECK();
+  }
+  std::vector<unsigned long long> h((size_t)(2 + ntasks));
+  BBTC_CUDA(cudaMemcpyAsync(h.data(), counters, sizeof(unsigned long long) * h.size(),
+                            cudaMemcpyDeviceToHost, s));
+  BBTC_CUDA(cudaStreamSynchronize(s));
+  if ((int32_t)h[1] != 0) {
+    set_error("bbtc_count_batch: the counting kernel passed its %u ms limit", timeout_ms);
+    return BBTC_ETIMEOUT;
+  }
+  for (int32_t i = 0; i < ng; ++i) {
+    uint64_t c = 0;
+    const int64_t b = task_base[(size_t)i];
+    for (int64_t t = 0; t < gs[i]->plan.ntasks; ++t) c += h[(size_t)(2 + b + t)];
+    counts[i] = c;
+  }
+  return BBTC_OK;
 }
 
 }  // namespace bbtc
@@ -545,6 +735,7 @@ extern "C" bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *c
       P.gid = nullptr;
       P.graph_count = nullptr;
       P.task_cycles = nullptr;
+      P.edge_sup = nullptr;
       P.status = reinterpret_cast<int32_t *>(scratch + NOALLOC_STATUS);
       P.timeout_ns = 0;
       const size_t smem = count_smem_bytes();

@@ -33,7 +33,7 @@ struct TaskDesc {
 // destination v) for task t = (i, j, k).
 struct WorkItem {
   int32_t task;
-  int32_t flags;  // bit 0: staged lists use the hash table (bbTC-HMap), else sorted search
+  int32_t flags;  // bits 0-1: 0 INTERSECT, 1 HASHMAP, 2 AUTO; bits 2..: AUTO hash threshold
   int64_t x0, x1;
 };
 
@@ -68,7 +68,7 @@ struct Plan {
   // counting scratch owned by the plan: [0] work-stealing head, [1] status,
   // [2] total, [3, 3+T) per-task counts, [3+T, 3+T+ng) per-graph counts
   unsigned long long *scratch = nullptr;
-  int blocks_per_sm[4] = {0, 0, 0, 0};  // occupancy of each counting-kernel mode
+  int blocks_per_sm[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // occupancy of each counting-kernel mode
   // streamed mode: the block arrays live in pinned host memory instead
   bool streamed = false;
   uint32_t *h_rp = nullptr;
@@ -139,20 +139,33 @@ void free_plan_host(Plan *pl);  // pinned host copies of a streamed plan
 bbtc_status configure_count_kernels(Plan *pl);
 
 // a9-a10: per-task counts (plan scratch, Alg. 4 order), optional per-vertex
-// counts by position (vertex_count, device, n) and per-graph counts (plan
-// scratch); the total goes to the plan scratch. Enqueues only.
+// counts by position (vertex_count, device, n), per-graph counts (plan
+// scratch) and per-edge support by position in pl.ci (edge_sup, device, m,
+// zeroed by the caller); the total goes to the plan scratch. Enqueues only.
 bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                       bool per_graph, uint32_t timeout_ms, cudaStream_t s,
                       cudaEvent_t ev_begin, cudaEvent_t ev_end,
-                      unsigned long long *task_cycles = nullptr);
+                      unsigned long long *task_cycles = nullptr, unsigned *edge_sup = nullptr);
 // The three parts of run_count: zero the outputs, drain items [item0,
 // item0 + nitems) in one persistent launch (accumulating), sum the tasks.
 bbtc_status count_reset(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                         bool per_graph, cudaStream_t s);
 bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t nitems,
                          unsigned long long *vertex_count, bool per_graph, uint32_t timeout_ms,
-                         cudaStream_t s, unsigned long long *task_cycles = nullptr);
+                         cudaStream_t s, unsigned long long *task_cycles = nullptr,
+                         unsigned *edge_sup = nullptr);
 bbtc_status count_finish(const Plan &pl, cudaStream_t s);
+
+// Counts the handles gs[0, ng) (each holding a resident plan) in one
+// persistent launch over all their work items; counts[i] is gs[i]'s total.
+// Reads the plans only. Synchronises s.
+bbtc_status count_plans(bbtc_graph *const *gs, int32_t ng, uint32_t timeout_ms, cudaStream_t s,
+                        uint64_t *counts);
+
+// Per-edge support from block-column order (pl.ci positions) to the order of
+// the oriented CSR's colidx (device arrays of g->m entries; resident plan).
+bbtc_status edge_support_to_csr(const bbtc_graph *g, const Plan &pl, const unsigned *by_block,
+                                unsigned *by_csr, cudaStream_t s);
 
 // a11: count with the blocks streamed from pinned host memory through a
 // device pool of `budget` bytes (two halves, double-buffered).

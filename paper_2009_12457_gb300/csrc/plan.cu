@@ -241,18 +241,13 @@ __global__ void k_item_fill(const int32_t *__restrict__ order, const int32_t *__
     const int t = order[x];
     const int i = tasks[3 * t], j = tasks[3 * t + 1], k = tasks[3 * t + 2];
     const int64_t b0 = boff[i * (p + 1) + j], b1 = boff[i * (p + 1) + j + 1];
-    // isDense (Alg. 7): staged lists N(G_jk, v) averaging more than the
-    // threshold use the hash table, shorter ones sorted search.
-    int32_t flags;
-    if (kernel_mode == BBTC_KERNEL_HASHMAP) {
-      flags = 1;
-    } else if (kernel_mode == BBTC_KERNEL_INTERSECT) {
-      flags = 0;
-    } else {
-      const int64_t vj = cuts[j + 1] - cuts[j];
-      const double djk = vj > 0 ? (double)block_nnz(boff, p, j, k) / (double)vj : 0.0;
-      flags = djk > (double)hash_threshold ? 1 : 0;
-    }
+    // isDense (Alg. 7), decided per staged list N(G_jk, v) by the counting
+    // kernel: bits 0-1 = 0 INTERSECT (sorted search), 1 HASHMAP, 2 AUTO;
+    // bits 2.. = the AUTO length above which a list that does not fit a
+    // bitmap is hashed rather than searched
+    const int32_t flags = kernel_mode == BBTC_KERNEL_HASHMAP     ? 1
+                          : kernel_mode == BBTC_KERNEL_INTERSECT ? 0
+                                                                 : 2 | (hash_threshold << 2);
     for (uint64_t c = 0; c < n_items; ++c) {
       WorkItem w;
       w.task = t;
@@ -261,6 +256,29 @@ __global__ void k_item_fill(const int32_t *__restrict__ order, const int32_t *__
       w.x1 = w.x0 + chunk < b1 ? w.x0 + chunk : b1;
       items[first[x] + c] = w;
     }
+  }
+}
+
+// Per-edge values from block-column order to oriented-CSR order: oriented
+// edge e = (u, v) sits in block (part(u), part(v)) at the run of row u that
+// starts at the first entry of the row at or above c_part(v).
+__global__ void k_edge_to_csr(const int32_t *__restrict__ esrc, const int32_t *__restrict__ colidx,
+                              const int64_t *__restrict__ rowptr, int64_t m,
+                              const int32_t *__restrict__ cuts_g, int p,
+                              const int64_t *__restrict__ rpb_g, const uint32_t *__restrict__ rp,
+                              const unsigned *__restrict__ by_block, unsigned *__restrict__ by_csr) {
+  __shared__ int32_t cuts[MAXP + 1];
+  __shared__ int64_t rpb[MAXP * MAXP];
+  for (int i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) rpb[i] = rpb_g[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = esrc[e], v = colidx[e];
+    const int a = part_of_dev(cuts, p, u), b = part_of_dev(cuts, p, v);
+    const int64_t run0 = lower_bound_dev<int32_t, int64_t>(colidx, rowptr[u], rowptr[u + 1], cuts[b]);
+    const int64_t slot = rpb[a * p + b] + (u - cuts[a]);
+    by_csr[e] = by_block[(int64_t)rp[slot] + (e - run0)];
   }
 }
 
@@ -501,6 +519,26 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   pl.bytes = (uint64_t)m * 16 + (uint64_t)pl.total_rp * 4 + (uint64_t)nt * (24 + sizeof(TaskDesc)) +
              (uint64_t)pl.nitems * sizeof(WorkItem) + (uint64_t)(SCR_TASKS + nt + g->ng) * 8;
   g->plan = pl;
+  return BBTC_OK;
+}
+
+bbtc_status edge_support_to_csr(const bbtc_graph *g, const Plan &pl, const unsigned *by_block,
+                                unsigned *by_csr, cudaStream_t s) {
+  if (pl.streamed || !pl.rp) {
+    set_error("internal: per-edge support needs a resident plan");
+    return BBTC_EINTERNAL;
+  }
+  if (g->m == 0) return BBTC_OK;
+  const int p = pl.p;
+  Scratch scratch(s);
+  int64_t *d_rpb = nullptr;
+  BBTC_TRY(scratch.get(&d_rpb, (int64_t)p * p));
+  BBTC_CUDA(cudaMemcpyAsync(d_rpb, pl.h_rpb, sizeof(int64_t) * (size_t)p * p,
+                            cudaMemcpyHostToDevice, s));
+  k_edge_to_csr<<<grid_for(g->m, 256, 32), 256, 0, s>>>(g->esrc, g->colidx, g->rowptr, g->m,
+                                                        pl.cuts, p, d_rpb, pl.rp, by_block,
+                                                        by_csr);
+  BBTC_LAUNCH_CHECK();
   return BBTC_OK;
 }
 

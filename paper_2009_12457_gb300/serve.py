@@ -1,16 +1,18 @@
 """Continuous-batching triangle-count server over the C ABI.
 
 Requests name a graph (any hashable key); a `source(key)` callable returns its
-host CSR. The server keeps prepared graphs resident (the oriented CSR built by
-bbtc_graph_create is the cache entry), admits a graph into device memory only
-while the cache stays under a byte budget (evicting unreferenced entries, least
-recently used first), and runs `workers` worker threads, each on its own CUDA
-stream. A worker that frees up takes every request that has arrived (up to
-`max_batch`), prepares the graphs that are not cached, and counts the whole
-batch with one bbtc_count_batch call (one persistent launch over the union of
-the batch's graphs). Requests that arrive while batches are on the GPU wait for
-the next free worker, so batches overlap on the device and new work is admitted
-as slots and memory free up.
+host CSR. The server keeps prepared graphs resident -- the cache entry is the
+handle that bbtc_graph_create built (the oriented CSR) together with the plan
+that bbtc_graph_plan built on it (blocks, tasks, work items) -- and admits a
+graph into device memory only while the cache stays under a byte budget
+(evicting unreferenced entries, least recently used first). `workers` worker
+threads run, each on its own CUDA stream. A worker that frees up takes every
+request that has arrived (up to `max_batch`), prepares the graphs that are not
+cached, and counts the whole batch with one bbtc_count_batch call: one
+persistent launch over the work items of all the batch's graphs, each read
+from its own cached plan. Requests that arrive while batches are on the GPU
+wait for the next free worker, so batches overlap on the device and new work
+is admitted as slots and memory free up.
 
 Counts are exact integers: a request's result does not depend on which batch
 it rode in.
@@ -24,8 +26,8 @@ import time
 
 import numpy as np
 
-from . import (Graph, bbtc_count, bbtc_count_batch, bbtc_graph_create_async,
-               bbtc_graph_destroy, bbtc_graph_get_info, make_opts)
+from . import (Graph, bbtc_count_batch, bbtc_graph_create_async, bbtc_graph_destroy,
+               bbtc_graph_get_info, bbtc_graph_plan, make_opts)
 
 
 class Request:
@@ -40,16 +42,15 @@ class Request:
 
 
 class _Entry:
-    __slots__ = ("handle", "bytes", "refs", "ready", "lock")
+    __slots__ = ("handle", "bytes", "refs", "ready")
 
     def __init__(self):
         self.handle = 0
         self.bytes = 0
         self.refs = 0
+        # set once the handle and its plan exist; from then on batch counts
+        # only read them, so workers on different streams may share the entry
         self.ready = threading.Event()
-        # a handle is not thread-safe: a direct count (which builds and uses
-        # the handle's plan) holds this lock; batch counts only read the handle
-        self.lock = threading.Lock()
 
 
 class Server:
@@ -69,6 +70,7 @@ class Server:
         self.stop = False
         self.done: list[Request] = []
         self.hits = self.misses = self.evictions = 0
+        self.errors: list[str] = []
         self.streams = [torch.cuda.Stream() for _ in range(workers)]
         self.threads = [threading.Thread(target=self._worker, args=(i,), daemon=True)
                         for i in range(workers)]
@@ -78,10 +80,10 @@ class Server:
     # ------------------------------------------------------------ cache
     @staticmethod
     def _estimate_bytes(n, nnz):
-        # oriented CSR (rowptr, colidx, esrc, perm, degree) plus the plan's
-        # in-edge arrays, from the input size
+        # oriented CSR (rowptr, colidx, esrc, perm, degree) and the plan
+        # (block columns, in-edges, row pointers), from the input size
         m = nnz // 2 + 1
-        return 8 * (n + 1) + 8 * n + 20 * m
+        return 28 * n + 24 * m
 
     def _acquire(self, key, stream):
         """Cache entry for key (creating the graph if missing); holds a reference."""
@@ -130,6 +132,11 @@ class Server:
         ent.bytes = need
         flags = 0x2 if self.symmetric else 0
         ent.handle = bbtc_graph_create_async(n, rowptr, colidx, flags, stream)
+        bbtc_graph_plan(ent.handle, make_opts(p=self.p, kernel=self.kernel, stream=stream))
+        actual = int(bbtc_graph_get_info(ent.handle)["device_bytes"])
+        with self.cv:
+            self.cache_bytes += actual - need
+            ent.bytes = actual
         ent.ready.set()
         return ent
 
@@ -157,19 +164,16 @@ class Server:
             acquired = []
             try:
                 with torch.cuda.stream(stream):
+                    handles = []
                     for r in batch:
-                        self._acquire(r.key, stream)
+                        handles.append(self._acquire(r.key, stream).handle)
                         acquired.append(r.key)
-                    handles = [self.cache[k].handle for k in acquired]
                     opts = make_opts(p=self.p, kernel=self.kernel, stream=stream)
-                    if len(handles) == 1:
-                        with self.cache[acquired[0]].lock:
-                            c = bbtc_count(handles[0], opts)
-                        counts = np.array([c], dtype=np.uint64)
-                        stats = np.zeros(1, dtype=np.int32)
-                    else:
-                        counts, stats = bbtc_count_batch(handles, opts)
-            except Exception:  # the batch fails as a whole; the server keeps running
+                    counts, stats = bbtc_count_batch(handles, opts)
+            except Exception as exc:  # the batch fails as a whole; the server keeps running
+                with self.cv:
+                    if len(self.errors) < 16:
+                        self.errors.append(f"{type(exc).__name__}: {exc}")
                 counts = np.zeros(len(batch), dtype=np.uint64)
                 stats = np.full(len(batch), 6, dtype=np.int32)
             t1 = time.perf_counter()

@@ -179,3 +179,38 @@ def test_per_task_cycles_and_estimator_study():
         s = workload.study(g, p=4, repeats=1)
         assert set(s["coverage"]) == {"nnz", "density", "degree", "bbtc"}
         assert all(0 < v <= 1.0 for c in s["coverage"].values() for v in c.values())
+
+
+def test_count_batch_each_handle_keeps_its_plan():
+    # resident batches count every handle through its own plan in one launch:
+    # automatic p per handle, repeated handles, mixed kernels, plans built
+    # earlier with other options, and the union path under a device budget
+    graphs = small_batch(17, k=20) + [graphgen.rmat(14, 16, 3), graphgen.rmat(13, 8, 4)]
+    expect = oracle_totals(graphs)
+    handles = [bb.bbtc_graph_create(*g) for g in graphs]
+    try:
+        bb.bbtc_graph_plan(handles[-1], bb.make_opts(p=7, kernel="hashmap"))
+        bb.bbtc_count(handles[-2], bb.make_opts(p=3))
+        for opts in (bb.make_opts(), bb.make_opts(p=5, kernel="intersect"),
+                     bb.make_opts(p=2, kernel="hashmap", chunk=16),
+                     bb.make_opts(p=3, device_budget_bytes=1 << 30)):
+            counts, stats = bb.bbtc_count_batch(handles, opts)
+            assert not stats.any()
+            assert np.array_equal(counts, expect)
+        twice = handles[-3:] + handles[-3:]
+        counts, _ = bb.bbtc_count_batch(twice, bb.make_opts(p=4))
+        assert np.array_equal(counts, np.concatenate([expect[-3:], expect[-3:]]))
+    finally:
+        for h in handles:
+            bb.bbtc_graph_destroy(h)
+
+
+def test_plan_then_async_without_a_count():
+    n, rp, ci = graphgen.rmat(12, 16, 8)
+    with bb.Graph(n, rp, ci) as g:
+        opts = bb.make_opts(p=3)
+        bb.bbtc_graph_plan(g.handle, opts)
+        total = torch.zeros(1, dtype=torch.int64, device="cuda")
+        bb.bbtc_count_async(g.handle, opts, total)
+        torch.cuda.synchronize()
+        assert int(total.item()) == oracle_totals([(n, rp, ci)])[0]

@@ -222,3 +222,36 @@ def test_rows_longer_than_the_shared_sort():
     with bb.Graph(*G.complete(k), symmetric=True) as dev:
         assert dev.info()["dplus_max"] == k - 1
         assert dev.count(p=3) == G.choose(k, 3)
+
+
+@pytest.mark.parametrize("p", [1, 3, 8])
+def test_per_edge_support_matches_oracle(p):
+    cases = [graphgen.rmat(12, 16, 5), G.complete(9), G.wheel(11), graphgen.gnm(3000, 40000, 4)]
+    for n, rp, ci in cases:
+        pr = oracle.prepare(n, rp, ci)
+        expect = oracle.edge_support(n, pr["rowptr"], pr["colidx"])
+        with bb.Graph(n, rp, ci) as g:
+            for kernel in ("auto", "intersect", "hashmap"):
+                out = g.count(p=p, kernel=kernel, per_edge=True, per_vertex=True)
+                assert np.array_equal(out["per_edge"], expect), (n, p, kernel)
+                assert int(out["per_edge"].sum()) == 3 * out["total"]
+        # the same edges seen from the original ids
+        with bb.Graph(n, rp, ci) as g:
+            u, v, s = g.edge_support(p=p)
+        assert np.array_equal(u, pr["perm"][np.repeat(np.arange(n), np.diff(pr["rowptr"]))])
+        assert np.array_equal(s, expect)
+
+
+def test_per_edge_support_large_sampled():
+    # scale 18: edges whose support the oracle recomputes one by one
+    n, rp, ci = graphgen.rmat(18, 16, 7)
+    with bb.Graph(n, rp, ci, symmetric=True) as g:
+        total = g.count(p=4)
+        u, v, s = g.edge_support(p=4)
+    assert int(s.sum()) == 3 * total
+    rng = np.random.default_rng(2)
+    for e in rng.choice(len(s), 200, replace=False):
+        a, b = int(u[e]), int(v[e])
+        na = set(ci[rp[a]:rp[a + 1]].tolist()) - {a}
+        nb = set(ci[rp[b]:rp[b + 1]].tolist()) - {b}
+        assert s[e] == len(na & nb), (a, b)
