@@ -70,7 +70,9 @@ typedef struct {
   uint64_t device_budget_bytes; /* 0 = blocks resident; else the counting step keeps at most
                                    this many bytes of blocks on the device, streaming them
                                    from pinned host memory (the plan's block arrays move
-                                   there); preparation itself still uses device memory */
+                                   there; their pinned buffers are kept for reuse by later
+                                   streamed plans, up to 64 GiB, until the process exits);
+                                   preparation itself still uses device memory */
   uint64_t *per_vertex_out;     /* NULL, or n uint64 (ORIGINAL ids): triangles at each vertex */
   uint64_t *per_task_out;       /* NULL, or bbtc_num_tasks(p) uint64 in Alg. 4 order */
   void *stream;                 /* cudaStream_t to run on; NULL = the handle's own stream */

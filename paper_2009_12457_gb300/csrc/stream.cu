@@ -3,15 +3,19 @@
 // When a caller gives bbtc_count a device budget, the plan's block arrays
 // (each block G_ab's row pointers and columns, and each block's in-edges) move
 // to pinned host memory. Tasks are then processed in the plan's order, in
-// rounds: a round is the longest run of consecutive tasks whose distinct
-// blocks fit in half of a device pool of `budget` bytes. While the tasks of
-// one round are counted on the compute stream, the blocks of the next round are
-// copied into the other half on a copy stream (the paper's prefetch of the next
-// task's blocks, Alg. 7), and each task's descriptor is rewritten to point at
-// its blocks' copies. Counts accumulate across rounds exactly as in one launch.
+// rounds. The device pool of `budget` bytes holds blocks at fixed offsets:
+// a round is the longest run of consecutive tasks whose blocks are either
+// already in the pool or fit beside the blocks of the round still being
+// counted. While one round is counted on the compute stream, the next round's
+// missing blocks are copied on a copy stream (the paper's prefetch of the next
+// task's blocks, Alg. 7); blocks that stay in the pool are not copied again.
+// Each task's descriptor is rewritten to point at its blocks in the pool.
+// Counts accumulate across rounds exactly as in one launch.
 #include <stdio.h>
 
+#include <algorithm>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -25,10 +29,66 @@ constexpr size_t ALIGN = 256;
 
 inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
+// Pinned host buffers are kept for reuse once a streamed plan lets them go:
+// pinning tens of GB costs seconds (page by page), far more than the copies,
+// and a caller that streams one graph after another needs buffers of the
+// same sizes again. A request takes the smallest cached buffer that holds it
+// and is at most twice its size; released buffers stay cached up to
+// PINNED_KEEP bytes in total, and the rest are freed.
+constexpr size_t PINNED_KEEP = 64ull << 30;
+
+struct PinnedCache {
+  std::mutex mu;
+  std::multimap<size_t, void *> free_by_size;
+  std::map<void *, size_t> size_of;
+  size_t cached = 0;
+};
+
+PinnedCache &pinned_cache() {
+  static PinnedCache *c = new PinnedCache;  // never destroyed: safe during exit
+  return *c;
+}
+
+cudaError_t pinned_alloc(void **ptr, size_t bytes) {
+  PinnedCache &c = pinned_cache();
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.free_by_size.lower_bound(bytes);
+    if (it != c.free_by_size.end() && it->first <= 2 * bytes) {
+      *ptr = it->second;
+      c.cached -= it->first;
+      c.free_by_size.erase(it);
+      return cudaSuccess;
+    }
+  }
+  cudaError_t e = cudaHostAlloc(ptr, bytes, cudaHostAllocDefault);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.size_of[*ptr] = bytes;
+  }
+  return e;
+}
+
+void pinned_release(void *ptr) {
+  if (!ptr) return;
+  PinnedCache &c = pinned_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  auto it = c.size_of.find(ptr);
+  if (it == c.size_of.end()) return;
+  const size_t bytes = it->second;
+  if (c.cached + bytes <= PINNED_KEEP) {
+    c.free_by_size.emplace(bytes, ptr);
+    c.cached += bytes;
+  } else {
+    c.size_of.erase(it);
+    cudaFreeHost(ptr);
+  }
+}
+
 template <typename T>
 bbtc_status to_pinned(T **host, T **dev, int64_t count, cudaStream_t s) {
   const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
-  BBTC_CUDA(cudaHostAlloc(reinterpret_cast<void **>(host), bytes, cudaHostAllocDefault));
+  BBTC_CUDA(pinned_alloc(reinterpret_cast<void **>(host), bytes));
   if (count > 0) BBTC_CUDA(cudaMemcpyAsync(*host, *dev, sizeof(T) * (size_t)count,
                                            cudaMemcpyDeviceToHost, s));
   return BBTC_OK;
@@ -73,11 +133,11 @@ struct Run {  // the work items of one task, in plan order
 }  // namespace
 
 void free_plan_host(Plan *pl) {
-  if (pl->h_rp) cudaFreeHost(pl->h_rp);
-  if (pl->h_ci) cudaFreeHost(pl->h_ci);
-  if (pl->h_ie_u) cudaFreeHost(pl->h_ie_u);
-  if (pl->h_ie_v) cudaFreeHost(pl->h_ie_v);
-  if (pl->h_ie_e) cudaFreeHost(pl->h_ie_e);
+  pinned_release(pl->h_rp);
+  pinned_release(pl->h_ci);
+  pinned_release(pl->h_ie_u);
+  pinned_release(pl->h_ie_v);
+  pinned_release(pl->h_ie_e);
   pl->h_rp = nullptr;
   pl->h_ci = nullptr;
   pl->h_ie_u = pl->h_ie_v = nullptr;
@@ -132,16 +192,27 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
     return 3 * align_up(4 * (size_t)(ie1(k.a, k.b) - ie0(k.a, k.b)));
   };
 
-  const size_t half = (size_t)(budget / 2) & ~(ALIGN - 1);
+  // The pool holds blocks at fixed offsets. A round's blocks that are already
+  // in the pool (copied for an earlier round and not overwritten since) are
+  // used in place; the others go to free space, where a block may overwrite
+  // only blocks that neither the round in flight nor this round uses. The
+  // copies of round r wait for the kernel of round r-2 (every kernel that may
+  // have read what they overwrite), so they overlap the kernel of round r-1.
+  const size_t pool_bytes = (size_t)budget & ~(ALIGN - 1);
   Scratch scratch(s);
   unsigned char *pool = nullptr;
-  BBTC_TRY(scratch.get(&pool, (int64_t)(2 * half)));
+  BBTC_TRY(scratch.get(&pool, (int64_t)pool_bytes));
+  struct Slot {
+    size_t off, size;
+    int64_t round;  // last round that uses the block
+  };
+  std::map<BlockKey, Slot> placed;
   cudaStream_t cs = nullptr;
   cudaEvent_t copy_done[2] = {nullptr, nullptr}, kern_done[2] = {nullptr, nullptr};
   cudaEvent_t t_begin = nullptr, t_end = nullptr;
-  TaskDesc *stage[2] = {nullptr, nullptr};  // pinned staging of descriptors per half
+  TaskDesc *stage[2] = {nullptr, nullptr};  // pinned staging of descriptors, by round parity
   bbtc_status st = BBTC_OK;
-  bool used_half[2] = {false, false};
+  bool used_parity[2] = {false, false};
   int64_t round = 0;
   float copy_ms_total = 0.f;
   do {
@@ -151,10 +222,10 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
         cudaEventCreate(&kern_done[0]) != cudaSuccess ||
         cudaEventCreate(&kern_done[1]) != cudaSuccess || cudaEventCreate(&t_begin) != cudaSuccess ||
         cudaEventCreate(&t_end) != cudaSuccess ||
-        cudaHostAlloc(reinterpret_cast<void **>(&stage[0]), sizeof(TaskDesc) * (size_t)(nt > 0 ? nt : 1),
-                      cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc(reinterpret_cast<void **>(&stage[1]), sizeof(TaskDesc) * (size_t)(nt > 0 ? nt : 1),
-                      cudaHostAllocDefault) != cudaSuccess) {
+        pinned_alloc(reinterpret_cast<void **>(&stage[0]),
+                     sizeof(TaskDesc) * (size_t)(nt > 0 ? nt : 1)) != cudaSuccess ||
+        pinned_alloc(reinterpret_cast<void **>(&stage[1]),
+                     sizeof(TaskDesc) * (size_t)(nt > 0 ? nt : 1)) != cudaSuccess) {
       set_error("streamed count: creating streams, events or staging buffers failed");
       st = BBTC_ECUDA;
       break;
@@ -163,42 +234,85 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
     if (cudaEventRecord(t_begin, s) != cudaSuccess) { st = BBTC_ECUDA; break; }
     size_t pos = 0;
     while (pos < runs.size() && st == BBTC_OK) {
-      // the longest run of tasks whose distinct blocks fit in one half
-      std::map<BlockKey, size_t> placed;
-      size_t used = 0, first = pos;
+      // place blocks for the longest run of tasks that fits next to the
+      // blocks of the round in flight (round - 1)
+      std::vector<std::pair<BlockKey, Slot>> fresh;  // blocks to copy this round
+      auto busy_until = [&](const Slot &sl) { return sl.round >= round - 1; };
+      auto find_gap = [&](size_t need, size_t *off) -> bool {
+        std::vector<std::pair<size_t, size_t>> used;  // protected intervals
+        for (const auto &kv : placed)
+          if (busy_until(kv.second)) used.emplace_back(kv.second.off, kv.second.off + kv.second.size);
+        for (const auto &f : fresh) used.emplace_back(f.second.off, f.second.off + f.second.size);
+        std::sort(used.begin(), used.end());
+        size_t at = 0;
+        for (const auto &iv : used) {
+          if (iv.first >= at + need) break;
+          if (iv.second > at) at = iv.second;
+        }
+        if (at + need > pool_bytes) return false;
+        *off = at;
+        return true;
+      };
+      const size_t first = pos;
       while (pos < runs.size()) {
         const int t = runs[pos].task;
         const BlockKey need[3] = {{1, ti[t], tj[t]}, {0, ti[t], tk[t]}, {0, tj[t], tk[t]}};
-        size_t add = 0;
-        bool fresh[3] = {false, false, false};
-        for (int q = 0; q < 3; ++q) {
-          bool dup = placed.count(need[q]) > 0;
-          for (int r = 0; r < q; ++r) dup = dup || (fresh[r] && !(need[r] < need[q]) && !(need[q] < need[r]));
-          if (!dup) {
-            fresh[q] = true;
-            add += block_bytes(need[q]);
+        const size_t nfresh0 = fresh.size();
+        bool ok = true;
+        for (int q = 0; q < 3 && ok; ++q) {
+          bool have = false;
+          for (const auto &f : fresh)
+            have = have || (!(f.first < need[q]) && !(need[q] < f.first));
+          if (have) continue;
+          auto it = placed.find(need[q]);
+          if (it != placed.end()) {
+            it->second.round = round;  // used in place: protected from now on
+            continue;
           }
+          size_t off = 0;
+          const size_t bytes = block_bytes(need[q]);
+          if (!find_gap(bytes, &off)) {
+            ok = false;
+            break;
+          }
+          // the new copy overwrites the (unprotected) blocks it overlaps
+          for (auto pit = placed.begin(); pit != placed.end();) {
+            const Slot &sl = pit->second;
+            if (sl.off < off + bytes && off < sl.off + sl.size)
+              pit = placed.erase(pit);
+            else
+              ++pit;
+          }
+          fresh.push_back({need[q], Slot{off, bytes, round}});
         }
-        if (used + add > half) break;
-        for (int q = 0; q < 3; ++q)
-          if (fresh[q]) {
-            placed[need[q]] = used;
-            used += block_bytes(need[q]);
-          }
+        if (!ok) {
+          fresh.resize(nfresh0);
+          break;
+        }
         ++pos;
       }
       if (pos == first) {
         const int t = runs[pos].task;
-        set_error("streamed count: the blocks of task (%d,%d,%d) do not fit in half of a %llu-byte "
+        if (round > 0 && !placed.empty()) {
+          // nothing fits beside the round in flight: let this round's copies
+          // wait for it, then plan with the whole pool
+          if (cudaStreamWaitEvent(cs, kern_done[(round - 1) & 1], 0) != cudaSuccess) {
+            st = BBTC_ECUDA;
+            break;
+          }
+          placed.clear();
+          continue;
+        }
+        set_error("streamed count: the blocks of task (%d,%d,%d) do not fit in a %llu-byte "
                   "device budget", ti[t], tj[t], tk[t], (unsigned long long)budget);
         st = BBTC_ENOMEM;
         break;
       }
+      for (const auto &f : fresh) placed[f.first] = f.second;
+
       const int h = (int)(round & 1);
-      unsigned char *base = pool + (size_t)h * half;
-      // the previous round in this half must have finished before its blocks
-      // and descriptor staging are overwritten
-      if (used_half[h]) {
+      // kernel round-2 read the regions now overwritten and used stage[h]
+      if (used_parity[h]) {
         if (cudaStreamWaitEvent(cs, kern_done[h], 0) != cudaSuccess ||
             cudaEventSynchronize(copy_done[h]) != cudaSuccess) {
           st = BBTC_ECUDA;
@@ -209,9 +323,9 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
       cudaEventCreate(&c0);
       cudaEventCreate(&c1);
       cudaEventRecord(c0, cs);
-      for (const auto &kv : placed) {
-        const BlockKey &k = kv.first;
-        unsigned char *dst = base + kv.second;
+      for (const auto &f : fresh) {
+        const BlockKey &k = f.first;
+        unsigned char *dst = pool + f.second.off;
         cudaError_t e1 = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess;
         if (k.kind == 0) {
           const int64_t nrp = vsize(k.a) + 1, c0i = col0(k.a, k.b), nci = col1(k.a, k.b) - c0i;
@@ -239,24 +353,24 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
         }
       }
       if (st != BBTC_OK) break;
-      // descriptors of the round's tasks, pointing into this half
+      // descriptors of the round's tasks, pointing at their blocks in the pool
       for (size_t r = first; r < pos; ++r) {
         const int t = runs[r].task;
         const int i = ti[t], j = tj[t], k = tk[t];
-        const size_t o_ie = placed[BlockKey{1, i, j}];
-        const size_t o_ik = placed[BlockKey{0, i, k}];
-        const size_t o_jk = placed[BlockKey{0, j, k}];
+        const size_t o_ie = placed[BlockKey{1, i, j}].off;
+        const size_t o_ik = placed[BlockKey{0, i, k}].off;
+        const size_t o_jk = placed[BlockKey{0, j, k}].off;
         const size_t seg = align_up(4 * (size_t)(ie1(i, j) - ie0(i, j)));
         TaskDesc &d = stage[h][t];
-        d.ie_u = reinterpret_cast<const int32_t *>(base + o_ie);
-        d.ie_v = reinterpret_cast<const int32_t *>(base + o_ie + seg);
-        d.ie_e = reinterpret_cast<const uint32_t *>(base + o_ie + 2 * seg);
+        d.ie_u = reinterpret_cast<const int32_t *>(pool + o_ie);
+        d.ie_v = reinterpret_cast<const int32_t *>(pool + o_ie + seg);
+        d.ie_e = reinterpret_cast<const uint32_t *>(pool + o_ie + 2 * seg);
         d.ie_off = ie0(i, j);
-        d.rp_ik = reinterpret_cast<const uint32_t *>(base + o_ik);
-        d.ci_ik = reinterpret_cast<const int32_t *>(base + o_ik + align_up(4 * (size_t)(vsize(i) + 1)));
+        d.rp_ik = reinterpret_cast<const uint32_t *>(pool + o_ik);
+        d.ci_ik = reinterpret_cast<const int32_t *>(pool + o_ik + align_up(4 * (size_t)(vsize(i) + 1)));
         d.ci_ik_off = col0(i, k);
-        d.rp_jk = reinterpret_cast<const uint32_t *>(base + o_jk);
-        d.ci_jk = reinterpret_cast<const int32_t *>(base + o_jk + align_up(4 * (size_t)(vsize(j) + 1)));
+        d.rp_jk = reinterpret_cast<const uint32_t *>(pool + o_jk);
+        d.ci_jk = reinterpret_cast<const int32_t *>(pool + o_jk + align_up(4 * (size_t)(vsize(j) + 1)));
         d.ci_jk_off = col0(j, k);
         d.c_i = pl.h_cuts[i];
         d.c_j = pl.h_cuts[j];
@@ -283,7 +397,7 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
         st = BBTC_ECUDA;
         break;
       }
-      used_half[h] = true;
+      used_parity[h] = true;
       ++round;
       // copy time of this round (host waits only for the copy, not the kernel)
       if (cudaEventSynchronize(c1) == cudaSuccess) {
@@ -310,8 +424,7 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
   stats->copy_ms = copy_ms_total;
   for (cudaEvent_t e : {copy_done[0], copy_done[1], kern_done[0], kern_done[1], t_begin, t_end})
     if (e) cudaEventDestroy(e);
-  for (TaskDesc *d : stage)
-    if (d) cudaFreeHost(d);
+  for (TaskDesc *d : stage) pinned_release(d);
   return st;
 }
 
