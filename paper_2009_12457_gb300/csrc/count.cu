@@ -86,13 +86,53 @@ __device__ __forceinline__ bool hash_contains(const int32_t *stage, int log2h, i
 // Per-batch lane records, shared by the warp: where each in-edge's probes
 // start in the flattened probe sequence and where they come from.
 struct LaneRec {
-  int64_t s0[32];    // first probe element (index into colidx) of each lane's in-edge
-  int64_t b0[32];    // N(G_jk, v) range of each lane (mixed batches only)
+  int64_t b0[32];     // N(G_jk, v) range of each lane (mixed batches only)
   int64_t b1[32];
+  uint32_t s0[32];    // first probe element (local column index) of each lane's in-edge
   uint32_t incl[32];  // inclusive prefix of the probe counts
   int32_t u[32];
   int32_t v[32];
 };
+
+// Runs the flattened probes of one batch: probe q (0 <= q < total) belongs to
+// the lane-record o whose inclusive prefix first exceeds q and reads column
+// rec.s0[o] + q - (prefix before o). Lane l takes q = l, l + 32, ...; U probes
+// per lane per round have their loads issued before any lookup, so each lane
+// keeps U global loads in flight. Column indices are local to the block
+// arrays and below 2^32.
+template <typename OnHit, typename Lookup>
+__device__ __forceinline__ void probe_batch(const int32_t *__restrict__ ci_ik, const LaneRec &rec,
+                                            uint32_t total, unsigned lane, OnHit &on_hit,
+                                            Lookup lookup) {
+  constexpr int U = 4;
+  int o = 0;
+  uint32_t o_end = rec.incl[0];
+  uint32_t addr = rec.s0[0];  // column of probe q is addr + q (mod 2^32)
+  for (uint32_t qb = lane; qb < total; qb += 32 * U) {
+    int32_t wv[U];
+    int own[U];
+    uint32_t qpos[U];
+#pragma unroll
+    for (int r = 0; r < U; ++r) {
+      const uint32_t q = qb + 32u * r;
+      own[r] = -1;
+      if (q < total) {
+        while (q >= o_end) {
+          ++o;
+          const uint32_t prev_end = o_end;
+          o_end = rec.incl[o];
+          addr = rec.s0[o] - prev_end;
+        }
+        qpos[r] = addr + q;
+        wv[r] = ci_ik[qpos[r]];
+        own[r] = o;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < U; ++r)
+      if (own[r] >= 0 && lookup(wv[r], own[r])) on_hit(wv[r], own[r], qpos[r]);
+  }
+}
 
 constexpr int UNIFORM_MIN = 4;  // a run of >= 4 in-edges into one v is a uniform batch
 
@@ -282,7 +322,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
       // flattened probes, interleaved over the lanes (lanes that share an
       // in-edge read consecutive elements); each lane's owner only moves
       // forward, at most 31 steps per batch
-      rec.s0[lane] = s0;
+      rec.s0[lane] = (uint32_t)s0;
       rec.incl[lane] = incl;
       if (!uniform) {
         rec.b0[lane] = b0;
@@ -293,80 +333,58 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         rec.v[lane] = uniform ? v0 : v;
       }
       __syncwarp();
+      uint32_t hits = 0;
       unsigned long long batch_hits = 0;  // one graph per uniform batch
-      int o = 0;
-      uint32_t o_end = rec.incl[0];
-      int64_t addr = rec.s0[0];  // ci_ik index of probe q is addr + q
-      // U probes per lane per round: their loads are issued before any
-      // lookup, so each lane keeps U global loads in flight
-      constexpr int U = 4;
-      for (uint32_t qb = lane; qb < total; qb += 32 * U) {
-        int32_t wv[U];
-        int own[U];
-        int64_t qpos[PER_EDGE ? U : 1];  // local column position of each probe
-#pragma unroll
-        for (int r = 0; r < U; ++r) {
-          const uint32_t q = qb + 32u * r;
-          own[r] = -1;
-          if (q < total) {
-            while (q >= o_end) {
-              ++o;
-              const uint32_t prev_end = o_end;
-              o_end = rec.incl[o];
-              addr = rec.s0[o] - (int64_t)prev_end;
-            }
-            wv[r] = ci_ik[addr + q];
-            own[r] = o;
-            if (PER_EDGE) qpos[r] = addr + q;
-          }
+      auto on_hit = [&](int32_t wv, int o, uint32_t qpos) {
+        ++hits;
+        if (PER_VERTEX) {
+          atomicAdd(&P.vcount[rec.u[o]], 1ull);
+          atomicAdd(&P.vcount[rec.v[o]], 1ull);
+          atomicAdd(&P.vcount[wv], 1ull);
         }
-#pragma unroll
-        for (int r = 0; r < U; ++r) {
-          if (own[r] < 0) continue;
-          bool hit;
-          if (staged) {
-            if (staged_mode == ST_BITMAP) {
-              const uint32_t d = (uint32_t)(wv[r] - staged_first);
-              hit = d < (uint32_t)staged_len &&
-                    ((reinterpret_cast<const unsigned *>(stage)[d >> 5] >> (d & 31u)) & 1u);
-            } else if (staged_mode == ST_HASH) {
-              hit = hash_contains(stage, staged_log2h, wv[r]);
-            } else {
-              hit = sorted_contains(stage, staged_len, wv[r]);
-            }
-          } else {
-            const int64_t lo = uniform ? b0 : rec.b0[own[r]];
-            const int64_t hi = uniform ? b1 : rec.b1[own[r]];
-            const int64_t pos = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, wv[r]);
-            hit = pos < hi && ci_jk[pos] == wv[r];
-          }
-          if (hit) {
-            ++acc;
-            if (PER_VERTEX) {
-              atomicAdd(&P.vcount[rec.u[own[r]]], 1ull);
-              atomicAdd(&P.vcount[rec.v[own[r]]], 1ull);
-              atomicAdd(&P.vcount[wv[r]], 1ull);
-            }
-            if (PER_EDGE) {
-              // the triangle's three edges, by position in the block columns:
-              // (u,v) from the in-edge record, (u,w) from the probe, (v,w)
-              // found in N(G_jk, v)
-              const int o = own[r];
-              const int64_t lo = uniform ? b0 : rec.b0[o];
-              const int64_t hi = uniform ? b1 : rec.b1[o];
-              const int64_t pvw = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, wv[r]);
-              atomicAdd(&P.edge_sup[ie_e[batch_x0 + o - ie_off]], 1u);
-              atomicAdd(&P.edge_sup[qpos[r] + ik_off], 1u);
-              atomicAdd(&P.edge_sup[pvw + jk_off], 1u);
-            }
-            if (PER_GRAPH) {
-              // every in-edge into v comes from v's own graph
-              if (uniform) ++batch_hits;
-              else atomicAdd(&P.graph_count[P.gid[rec.v[own[r]]]], 1ull);
-            }
-          }
+        if (PER_EDGE) {
+          // the triangle's three edges, by position in the block columns:
+          // (u,v) from the in-edge record, (u,w) from the probe, (v,w) found
+          // in N(G_jk, v)
+          const int64_t lo = uniform ? b0 : rec.b0[o];
+          const int64_t hi = uniform ? b1 : rec.b1[o];
+          const int64_t pvw = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, wv);
+          atomicAdd(&P.edge_sup[ie_e[batch_x0 + o - ie_off]], 1u);
+          atomicAdd(&P.edge_sup[(int64_t)qpos + ik_off], 1u);
+          atomicAdd(&P.edge_sup[pvw + jk_off], 1u);
         }
+        if (PER_GRAPH) {
+          // every in-edge into v comes from v's own graph
+          if (uniform) ++batch_hits;
+          else atomicAdd(&P.graph_count[P.gid[rec.v[o]]], 1ull);
+        }
+      };
+      // the probe loop, specialised by how N(G_jk, v) is looked up
+      if (staged && staged_mode == ST_BITMAP) {
+        const unsigned *__restrict__ bm = reinterpret_cast<const unsigned *>(stage);
+        const int32_t first = staged_first;
+        const uint32_t span = (uint32_t)staged_len;
+        probe_batch(ci_ik, rec, total, lane, on_hit, [&](int32_t w, int) {
+          const uint32_t dlt = (uint32_t)(w - first);
+          return dlt < span && ((bm[dlt >> 5] >> (dlt & 31u)) & 1u);
+        });
+      } else if (staged && staged_mode == ST_HASH) {
+        const int log2h = staged_log2h;
+        probe_batch(ci_ik, rec, total, lane, on_hit,
+                    [&](int32_t w, int) { return hash_contains(stage, log2h, w); });
+      } else if (staged) {
+        const int slen = staged_len;
+        probe_batch(ci_ik, rec, total, lane, on_hit,
+                    [&](int32_t w, int) { return sorted_contains(stage, slen, w); });
+      } else {
+        probe_batch(ci_ik, rec, total, lane, on_hit, [&](int32_t w, int o) {
+          const int64_t lo = uniform ? b0 : rec.b0[o];
+          const int64_t hi = uniform ? b1 : rec.b1[o];
+          const int64_t pos = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, w);
+          return pos < hi && ci_jk[pos] == w;
+        });
       }
+      acc += hits;
       if (PER_GRAPH && uniform) {
         batch_hits = warp_sum(batch_hits);
         if (lane == 0 && batch_hits) atomicAdd(&P.graph_count[P.gid[v0]], batch_hits);

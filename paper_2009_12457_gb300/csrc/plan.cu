@@ -36,61 +36,76 @@ __global__ void k_cuts(const int64_t *__restrict__ rowptr, int64_t n, int p,
   cuts[i] = c;
 }
 
-// In-edge keys for the oriented edge e = (u, v). Packed form (when
-// nb + bits(p) <= 32): key ((part(u) << nb | v) << 32) | u, value = the edge's
-// block position, sorted on the upper half only so u rides along. Otherwise
-// key (part(u) << nb) | v, value e.
-__global__ void k_inedge_keys(const int32_t *__restrict__ colidx,
-                              const int32_t *__restrict__ esrc,
-                              const uint32_t *__restrict__ pos_of_edge, int64_t m,
-                              const int32_t *__restrict__ cuts_g, int p, int nb, bool packed,
-                              uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-  __shared__ int32_t cuts[MAXP + 1];
-  for (int i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
-  __syncthreads();
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = esrc[e];
-    const uint64_t group = ((uint64_t)part_of_dev(cuts, p, u) << nb) | (uint64_t)colidx[e];
-    if (packed) {
-      keys[e] = (group << 32) | (uint64_t)(uint32_t)u;
-      vals[e] = pos_of_edge[e];
-    } else {
-      keys[e] = group;
-      vals[e] = (uint32_t)e;
+// In-edges of part a (the edges of rows V_a, positions [rowptr[c_a],
+// rowptr[c_a+1]) of the oriented CSR) grouped by destination v: a counting
+// sort on v - c_a. Step 1 counts the edges into each v (warp-aggregated:
+// lanes with equal v add once).
+__global__ void k_inedge_count(const int64_t *__restrict__ rowptr,
+                               const int32_t *__restrict__ colidx,
+                               const int32_t *__restrict__ cuts, int a,
+                               unsigned long long *__restrict__ hist) {
+  const int32_t c_a = cuts[a];
+  const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
+  const unsigned lane = threadIdx.x & 31u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = e0 + (int64_t)blockIdx.x * blockDim.x; base < e1; base += stride) {
+    const int64_t e = base + threadIdx.x;
+    const int32_t key = e < e1 ? colidx[e] - c_a : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == (unsigned)(__ffs(peers) - 1))
+      atomicAdd(&hist[key], (unsigned long long)__popc(peers));
+  }
+}
+
+// Step 2 (after an exclusive scan of the counts): the block offsets of part a,
+// boff[a*(p+1)+j] = first in-edge of part a whose destination is >= c_j.
+__global__ void k_inedge_offsets(const int64_t *__restrict__ rowptr,
+                                 const int32_t *__restrict__ cuts, int a, int p,
+                                 const unsigned long long *__restrict__ scan, int64_t bins,
+                                 int64_t *__restrict__ boff) {
+  const int j = threadIdx.x;
+  if (j > p) return;
+  const int32_t c_a = cuts[a];
+  const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
+  int64_t off;
+  if (j <= a) {
+    off = e0;
+  } else {
+    const int64_t idx = (int64_t)cuts[j] - c_a;  // scan has bins = n - c_a entries
+    off = idx < bins ? e0 + (int64_t)scan[idx] : e1;
+  }
+  boff[a * (p + 1) + j] = off;
+}
+
+// Step 3: scatter each edge of part a to its destination's run; within a run
+// the order of the sources is whatever the atomics give (counts do not depend
+// on it).
+__global__ void k_inedge_scatter(const int64_t *__restrict__ rowptr,
+                                 const int32_t *__restrict__ colidx,
+                                 const int32_t *__restrict__ esrc,
+                                 const uint32_t *__restrict__ pos_of_edge,
+                                 const int32_t *__restrict__ cuts, int a,
+                                 unsigned long long *__restrict__ offs,
+                                 int32_t *__restrict__ ie_u, int32_t *__restrict__ ie_v,
+                                 uint32_t *__restrict__ ie_e) {
+  const int32_t c_a = cuts[a];
+  const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
+  const unsigned lane = threadIdx.x & 31u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = e0 + (int64_t)blockIdx.x * blockDim.x; base < e1; base += stride) {
+    const int64_t e = base + threadIdx.x;
+    const int32_t key = e < e1 ? colidx[e] - c_a : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long b = 0;
+    if (key >= 0 && (int)lane == leader) b = atomicAdd(&offs[key], (unsigned long long)__popc(peers));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    if (key >= 0) {
+      const int64_t x = e0 + (int64_t)b + __popc(peers & ((1u << lane) - 1u));
+      ie_u[x] = esrc[e];
+      ie_v[x] = key + c_a;
+      ie_e[x] = pos_of_edge[e];
     }
-  }
-}
-
-__global__ void k_inedge_unpack(const uint64_t *__restrict__ keys,
-                                const uint32_t *__restrict__ vals, int64_t m, int nb,
-                                int32_t *__restrict__ ie_u, int32_t *__restrict__ ie_v,
-                                uint32_t *__restrict__ ie_e) {
-  const uint64_t mask = (1ull << nb) - 1ull;
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = keys[x];
-    ie_u[x] = (int32_t)(uint32_t)k;
-    ie_v[x] = (int32_t)((k >> 32) & mask);
-    ie_e[x] = vals[x];
-  }
-}
-
-// In-edges from the sorted keys; the edge's position becomes its position in
-// the block-major column array (pos_of_edge).
-__global__ void k_inedge_finish(const uint64_t *__restrict__ keys,
-                                const uint32_t *__restrict__ vals, int64_t m, int nb,
-                                const int32_t *__restrict__ esrc,
-                                const uint32_t *__restrict__ pos_of_edge,
-                                int32_t *__restrict__ ie_u, int32_t *__restrict__ ie_v,
-                                uint32_t *__restrict__ ie_e) {
-  const uint64_t mask = (1ull << nb) - 1ull;
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t e = vals[x];
-    ie_v[x] = (int32_t)(keys[x] & mask);
-    ie_e[x] = pos_of_edge[e];
-    ie_u[x] = esrc[e];
   }
 }
 
@@ -157,17 +172,6 @@ __global__ void k_bcsr_rowptr(const uint64_t *__restrict__ pos, int64_t total,
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x)
     rp[i] = (uint32_t)pos[i];
-}
-
-// boff[i*(p+1)+j] = first in-edge of part i whose destination is >= c_j.
-__global__ void k_block_offsets(const uint64_t *__restrict__ keys, int64_t m,
-                                const int32_t *__restrict__ cuts, int p, int nb, int shift,
-                                int64_t *__restrict__ boff) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= p * (p + 1)) return;
-  const int i = idx / (p + 1), j = idx % (p + 1);
-  const uint64_t target = (((uint64_t)i << nb) + (uint64_t)cuts[j]) << shift;
-  boff[idx] = lower_bound_dev<uint64_t, int64_t>(keys, 0, m, target);
 }
 
 __device__ __forceinline__ int64_t block_nnz(const int64_t *boff, int p, int i, int j) {
@@ -389,53 +393,55 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   k_bcsr_rowptr<<<grid_for(pl.total_rp, 256, 32), 256, 0, s>>>(cnt, pl.total_rp, pl.rp);
   PLAN_TRY(launch_status("build_plan"));
 
-  // in-edges grouped by (part(u), v, u), and the block offsets
-  uint64_t *ka = nullptr, *kb = nullptr;
-  uint32_t *va = nullptr, *vb = nullptr;
-  PLAN_TRY(scratch.get(&ka, m));
-  PLAN_TRY(scratch.get(&kb, m));
-  PLAN_TRY(scratch.get(&va, m));
-  PLAN_TRY(scratch.get(&vb, m));
+  // in-edges grouped by (part(u), v), and the block offsets: one counting
+  // sort on the destination per part
   PLAN_TRY(dalloc_n(&pl.ie_u, m, s));
   PLAN_TRY(dalloc_n(&pl.ie_v, m, s));
   PLAN_TRY(dalloc_n(&pl.ie_e, m, s));
   PLAN_TRY(dalloc_n(&pl.boff, (int64_t)p * (p + 1), s));
-  const int pbits = ceil_log2_u64((uint64_t)p);
-  const bool packed = nb + pbits <= 32;
-  const int shift = packed ? 32 : 0;
-  bool in_alt = false;
-  if (m > 0) {
-    k_inedge_keys<<<grid_for(m, 256, 32), 256, 0, s>>>(g->colidx, g->esrc, pos_of_edge, m,
-                                                        pl.cuts, p, nb, packed, ka, va);
-    PLAN_TRY(launch_status("build_plan"));
-    PLAN_TRY(radix_sort(ka, kb, va, vb, m, shift, shift + nb + pbits, s, &in_alt));
-    if (packed) {
-      k_inedge_unpack<<<grid_for(m, 256, 32), 256, 0, s>>>(in_alt ? kb : ka, in_alt ? vb : va,
-                                                            m, nb, pl.ie_u, pl.ie_v, pl.ie_e);
-    } else {
-      k_inedge_finish<<<grid_for(m, 256, 32), 256, 0, s>>>(in_alt ? kb : ka, in_alt ? vb : va,
-                                                            m, nb, g->esrc, pos_of_edge, pl.ie_u,
-                                                            pl.ie_v, pl.ie_e);
+  {
+    unsigned long long *hist = nullptr;
+    PLAN_TRY(scratch.get(&hist, n + 1));
+    for (int a = 0; a < p; ++a) {
+      const int64_t bins = n - pl.h_cuts[a];
+      if (cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (size_t)(bins + 1), s) !=
+          cudaSuccess) {
+        set_error("build_plan: cudaMemsetAsync failed");
+        free_plan(&pl, s);
+        return BBTC_ECUDA;
+      }
+      const int64_t part_edges_hint = m / p + 1;
+      if (m > 0) {
+        k_inedge_count<<<grid_for(part_edges_hint, 256, 32), 256, 0, s>>>(g->rowptr, g->colidx,
+                                                                        pl.cuts, a, hist);
+        PLAN_TRY(launch_status("build_plan"));
+      }
+      if (bins > 0)
+        PLAN_TRY(exclusive_scan_u64(reinterpret_cast<uint64_t *>(hist),
+                                    reinterpret_cast<uint64_t *>(hist), bins, s));
+      k_inedge_offsets<<<1, MAXP + 1, 0, s>>>(g->rowptr, pl.cuts, a, p, hist, bins, pl.boff);
+      PLAN_TRY(launch_status("build_plan"));
+      if (m > 0) {
+        k_inedge_scatter<<<grid_for(part_edges_hint, 256, 32), 256, 0, s>>>(
+            g->rowptr, g->colidx, g->esrc, pos_of_edge, pl.cuts, a, hist, pl.ie_u, pl.ie_v,
+            pl.ie_e);
+        PLAN_TRY(launch_status("build_plan"));
+      }
     }
-    PLAN_TRY(launch_status("build_plan"));
   }
-  k_block_offsets<<<(p * (p + 1) + 127) / 128, 128, 0, s>>>(in_alt ? kb : ka, m, pl.cuts, p, nb,
-                                                            shift, pl.boff);
-  PLAN_TRY(launch_status("build_plan"));
 
   // a7 + a8: tasks, estimates, order
   const int64_t nt = pl.ntasks;
   PLAN_TRY(dalloc_n(&pl.tasks, 3 * nt, s));
   PLAN_TRY(dalloc_n(&pl.est, nt, s));
   PLAN_TRY(dalloc_n(&pl.order, nt, s));
-  uint64_t *okeys = ka, *okeys_alt = kb;  // reuse (m may be < nt: allocate if needed)
-  uint32_t *ovals = va, *ovals_alt = vb;
-  if (nt > m) {
-    PLAN_TRY(scratch.get(&okeys, nt));
-    PLAN_TRY(scratch.get(&okeys_alt, nt));
-    PLAN_TRY(scratch.get(&ovals, nt));
-    PLAN_TRY(scratch.get(&ovals_alt, nt));
-  }
+  uint64_t *okeys = nullptr, *okeys_alt = nullptr;
+  uint32_t *ovals = nullptr, *ovals_alt = nullptr;
+  PLAN_TRY(scratch.get(&okeys, nt));
+  PLAN_TRY(scratch.get(&okeys_alt, nt));
+  PLAN_TRY(scratch.get(&ovals, nt));
+  PLAN_TRY(scratch.get(&ovals_alt, nt));
+  bool in_alt = false;
   k_tasks<<<(p * p * p + 127) / 128, 128, 0, s>>>(pl.boff, pl.cuts, p, pl.tasks, pl.est, okeys,
                                                   ovals);
   PLAN_TRY(launch_status("build_plan"));

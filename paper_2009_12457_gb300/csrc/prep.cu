@@ -290,6 +290,8 @@ __global__ void k_tile_rows(const int64_t *__restrict__ rowptr, int64_t n, int64
 // degree of u += first copies of v != u, flag unsorted rows and out-of-range
 // ids. MODE 1: out-degree at rank(u) += first copies with rank(v) > rank(u).
 // MODE 2: scatter rank(v) into row rank(u) (any order; rows are sorted after).
+// For a batch (voff != nullptr), the entries of a row of graph g are local ids
+// in [0, voff[g+1] - voff[g]), shifted here by voff[g].
 template <int MODE>
 __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ rowptr,
                                                     const int32_t *__restrict__ colidx, int64_t n,
@@ -302,7 +304,8 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
                                                     unsigned int *__restrict__ cursor,
                                                     int32_t *__restrict__ colidx_o,
                                                     int32_t *__restrict__ esrc_o,
-                                                    int32_t *__restrict__ err) {
+                                                    int32_t *__restrict__ err,
+                                                    const int64_t *__restrict__ voff, int ng) {
   const unsigned lane = threadIdx.x & 31u;
   const int64_t ntiles = (nnz + SP_TILE - 1) / SP_TILE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -313,6 +316,18 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
     int64_t u = first < t1 ? row_of_first(rowptr, n, first, rlo, rhi + 1) : rlo;
     int64_t row_end = rowptr[u + 1];
     int32_t ru = MODE > 0 ? rank[u] : 0;
+    int gi = 0;
+    int64_t gbase = 0, gend = n;
+    if (voff) {
+      int lo = 0, hi = ng;  // last graph with voff[lo] <= u
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (voff[mid] <= u) lo = mid; else hi = mid;
+      }
+      gi = lo;
+      gbase = voff[gi];
+      gend = voff[gi + 1];
+    }
 #pragma unroll
     for (int i = 0; i < SP_ITEMS; ++i) {
       const int64_t e = first + i;
@@ -325,14 +340,23 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
           row_end = rowptr[u + 1];
           if (MODE > 0) ru = rank[u];
         }
-        v = colidx[e];
+        if (voff) {
+          while (u >= gend && gi + 1 < ng) {
+            ++gi;
+            gbase = voff[gi];
+            gend = voff[gi + 1];
+          }
+        }
+        const int32_t vl = colidx[e];  // local to the row's graph
         first_in_row = e == rowptr[u];
         const int32_t prev = first_in_row ? -1 : colidx[e - 1];
+        const bool in_range = vl >= 0 && (int64_t)vl < gend - gbase;
         if (MODE == 0) {
-          if (v < 0 || v >= n) atomicOr(err, 2);
-          else if (!first_in_row && prev > v) atomicOr(err, 4);
+          if (!in_range) atomicOr(err, 2);
+          else if (!first_in_row && prev > vl) atomicOr(err, 4);
         }
-        head = v >= 0 && v < n && v != u && (first_in_row || prev != v);
+        v = in_range ? (int32_t)(vl + gbase) : 0;
+        head = in_range && v != u && (first_in_row || prev != vl);
       }
       if (MODE == 0) {
         const int64_t key = head ? u : -1;
@@ -378,9 +402,61 @@ __global__ void k_pair_unkey(const uint64_t *__restrict__ keys, int64_t m, int n
     colidx[e] = (int32_t)(keys[e] & mask);
 }
 
-// Sort every oriented row ascending: one warp per row, rows of up to 32 in
-// registers (bitonic network over shuffles), longer rows (up to SEG_CAP) in the
-// warp's shared memory (bitonic network, padded to a power of two).
+// Bitonic sort of 32*K values held by a warp in registers: element i of the
+// sequence is x[i / 32] of lane i % 32. Exchanges at distance j < 32 go
+// through shuffles, those at distance j >= 32 stay within a lane (slots r and
+// r ^ j/32).
+template <int K>
+__device__ __forceinline__ void warp_bitonic(int32_t (&x)[K], unsigned lane) {
+  constexpr int S = 32 * K;
+#pragma unroll
+  for (int k = 2; k <= S; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const int q = r ^ (j >> 5);
+          if (q > r) {
+            const bool up = (((int)lane + 32 * r) & k) == 0;
+            const int32_t a = x[r], b = x[q];
+            const bool swap = up ? (a > b) : (a < b);
+            x[r] = swap ? b : a;
+            x[q] = swap ? a : b;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const int32_t y = __shfl_xor_sync(0xffffffffu, x[r], j);
+          const bool up = (((int)lane + 32 * r) & k) == 0;
+          const bool lower = (lane & (unsigned)j) == 0;
+          x[r] = (lower == up) ? min(x[r], y) : max(x[r], y);
+        }
+      }
+    }
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void sort_row_regs(int32_t *__restrict__ row, int len, unsigned lane) {
+  int32_t x[K];
+#pragma unroll
+  for (int r = 0; r < K; ++r) {
+    const int i = (int)lane + 32 * r;
+    x[r] = i < len ? row[i] : INT_MAX;
+  }
+  warp_bitonic<K>(x, lane);
+#pragma unroll
+  for (int r = 0; r < K; ++r) {
+    const int i = (int)lane + 32 * r;
+    if (i < len) row[i] = x[r];
+  }
+}
+
+// Sort every oriented row ascending: one warp per row. Rows of up to 1024 are
+// sorted in registers (bitonic network over shuffles and register slots,
+// padded to 32 * 2^t), longer rows (up to SEG_CAP) in the warp's shared memory.
 constexpr int SR_WARPS = 4;
 
 __global__ void __launch_bounds__(SR_WARPS * 32) k_sort_rows(const int64_t *__restrict__ rowptr,
@@ -395,20 +471,23 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sort_rows(const int64_t *__re
     const int64_t b = rowptr[r];
     const int len = (int)(rowptr[r + 1] - b);
     if (len <= 1) continue;
+    int32_t *row = colidx + b;
     if (len <= 32) {
-      int32_t x = (int)lane < len ? colidx[b + lane] : INT_MAX;
-      for (int k = 2; k <= 32; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
-          const bool up = ((lane & k) == 0);
-          const bool lower = (lane & j) == 0;
-          x = (lower == up) ? min(x, y) : max(x, y);
-        }
-      if ((int)lane < len) colidx[b + lane] = x;
+      sort_row_regs<1>(row, len, lane);
+    } else if (len <= 64) {
+      sort_row_regs<2>(row, len, lane);
+    } else if (len <= 128) {
+      sort_row_regs<4>(row, len, lane);
+    } else if (len <= 256) {
+      sort_row_regs<8>(row, len, lane);
+    } else if (len <= 512) {
+      sort_row_regs<16>(row, len, lane);
+    } else if (len <= 1024) {
+      sort_row_regs<32>(row, len, lane);
     } else {
       int size = 64;
       while (size < len) size <<= 1;
-      for (int i = lane; i < size; i += 32) sm[i] = i < len ? colidx[b + i] : INT_MAX;
+      for (int i = lane; i < size; i += 32) sm[i] = i < len ? row[i] : INT_MAX;
       __syncwarp();
       for (int k = 2; k <= size; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -425,7 +504,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sort_rows(const int64_t *__re
           }
           __syncwarp();
         }
-      for (int i = lane; i < len; i += 32) colidx[b + i] = sm[i];
+      for (int i = lane; i < len; i += 32) row[i] = sm[i];
       __syncwarp();
     }
   }
@@ -453,7 +532,8 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   BBTC_LAUNCH_CHECK();
   const unsigned grid = grid_for(ntiles, 1, 32);
   k_sym_pass<0><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, g->deg, nullptr,
-                                       nullptr, nullptr, nullptr, nullptr, nullptr, err);
+                                       nullptr, nullptr, nullptr, nullptr, nullptr, err, g->voff,
+                                       g->ng);
   BBTC_LAUNCH_CHECK();
   int32_t herr = 0;
   BBTC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -490,6 +570,12 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
                       s, &in_alt));
   k_rank_finish<<<grid_for(n, 256, 16), 256, 0, s>>>(in_alt ? rk_alt : rk, n, nb, g->perm, rank);
   BBTC_LAUNCH_CHECK();
+  if (g->voff) {
+    BBTC_TRY(dalloc_n(&g->gid, n, s));
+    g->bytes += (uint64_t)n * sizeof(int32_t);
+    k_graph_of_position<<<grid_for(n, 256, 16), 256, 0, s>>>(g->perm, n, g->voff, g->ng, g->gid);
+    BBTC_LAUNCH_CHECK();
+  }
 
   // a4: out-degrees by rank, offsets, scatter, per-row sort
   BBTC_TRY(dalloc_n(&g->rowptr, n + 1, s));
@@ -497,7 +583,7 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   BBTC_CUDA(cudaMemsetAsync(g->rowptr, 0, sizeof(int64_t) * (size_t)(n + 1), s));
   k_sym_pass<1><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, nullptr, rank,
                                        reinterpret_cast<unsigned long long *>(g->rowptr),
-                                       nullptr, nullptr, nullptr, nullptr, err);
+                                       nullptr, nullptr, nullptr, nullptr, err, g->voff, g->ng);
   BBTC_LAUNCH_CHECK();
   int64_t *stats = nullptr;
   BBTC_TRY(scratch.get(&stats, 2));
@@ -522,7 +608,8 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   BBTC_TRY(scratch.get(&cursor, n));
   BBTC_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned int) * (size_t)(n > 0 ? n : 1), s));
   k_sym_pass<2><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, nullptr, rank,
-                                       nullptr, g->rowptr, cursor, g->colidx, g->esrc, err);
+                                       nullptr, g->rowptr, cursor, g->colidx, g->esrc, err,
+                                       g->voff, g->ng);
   BBTC_LAUNCH_CHECK();
   if (m > 0) {
     if (g->dplus_max <= SEG_CAP) {
@@ -563,7 +650,7 @@ bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t 
   }
 
   // ---- symmetric input with sorted rows: per-row path, no global sort
-  if (symmetric && !g->voff && nnz > 0) {
+  if (symmetric && nnz > 0) {
     bool applied = false;
     BBTC_TRY(prepare_sym_sorted(g, d_rowptr, d_colidx, nnz, err, &applied));
     if (applied) return BBTC_OK;

@@ -91,3 +91,31 @@ def study(graph: Graph, p: int, kernel: str = "auto", repeats: int = 3) -> dict:
         "coverage": {name: coverage(e, cycles) for name, e in est.items()},
         "spearman": {name: spearman(e[worked], cycles[worked]) for name, e in est.items()},
     }
+
+
+def main(argv=None):
+    """Run the study on a seeded R-MAT graph and print one JSON line."""
+    import argparse
+    import json
+
+    import graphgen
+
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--scale", type=int, default=21)
+    ap.add_argument("--edge-factor", type=int, default=16)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--p", default="8,16")
+    ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--repeats", type=int, default=3)
+    a = ap.parse_args(argv)
+    n, rp, ci = graphgen.rmat(a.scale, a.edge_factor, a.seed)
+    with Graph(n, rp, ci, symmetric=True) as g:
+        for p in (int(x) for x in a.p.split(",")):
+            r = study(g, p, a.kernel, a.repeats)
+            r.update({"graph": f"R-MAT scale {a.scale}, edge factor {a.edge_factor}, seed {a.seed}",
+                      "kernel": a.kernel})
+            print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -214,3 +214,30 @@ def test_plan_then_async_without_a_count():
         bb.bbtc_count_async(g.handle, opts, total)
         torch.cuda.synchronize()
         assert int(total.item()) == oracle_totals([(n, rp, ci)])[0]
+
+
+def test_symmetric_batch_fast_path_matches_oracle():
+    # symmetric batches with sorted rows take the per-row preparation path;
+    # each graph keeps its own order and orientation inside the union
+    graphs = [graphgen.rmat(s, 8 + 2 * s, 40 + s) for s in range(5, 12)]
+    graphs += [graphgen.gnm(n, 6 * n, n) for n in (10, 200, 3000)]
+    graphs.append((4, np.zeros(5, dtype=np.int64), np.zeros(0, dtype=np.int32)))
+    graphs.append(G.complete(40))
+    expect = oracle_totals(graphs)
+    with bb.BatchGraph(graphs, symmetric=True) as batch:
+        for p in (1, 3):
+            out = batch.count(p=p, per_graph=True, per_vertex=True)
+            assert np.array_equal(out["per_graph"], expect)
+        o = batch.oriented()
+        with bb.BatchGraph(graphs) as general:
+            og = general.oriented()
+        assert np.array_equal(o["rowptr"], og["rowptr"])
+        assert np.array_equal(o["colidx"], og["colidx"])
+        assert np.array_equal(o["perm"], og["perm"])
+    # an entry outside its own graph is rejected on this path too
+    voff = np.array([0, 3, 6], dtype=np.int64)
+    rowptr = np.array([0, 1, 2, 3, 4, 5, 6], dtype=np.int64)
+    colidx = np.array([1, 2, 0, 1, 2, 3], dtype=np.int32)
+    with pytest.raises(bb.BbtcError) as e:
+        bb.bbtc_graph_create_batch(voff, rowptr, colidx, bb.INPUT_SYMMETRIC)
+    assert e.value.status == 1
