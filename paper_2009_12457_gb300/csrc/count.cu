@@ -12,6 +12,7 @@
 // Work: a persistent grid; each warp takes work items (task, in-edge range)
 // from a global counter, heaviest task first, until none remain.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "graph.cuh"
@@ -49,6 +50,10 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Per-warp shared staging area for N(G_jk, v) (int32 slots).
 constexpr int STAGE = 2048;
+static_assert(STAGE % 4 == 0, "the bitmap is cleared with 16-byte stores");
+// largest power of two <= STAGE: the biggest hash table the stage holds
+constexpr int STAGE_POW2 = STAGE >= 2048 ? 2048 : STAGE >= 1024 ? 1024 : STAGE >= 512 ? 512 : 256;
+static_assert(STAGE_POW2 <= STAGE && STAGE >= 256, "stage too small");
 constexpr int MIN_STAGE = 8;
 constexpr int ST_NONE = 0, ST_SORTED = 1, ST_HASH = 2, ST_BITMAP = 3;
 constexpr int32_t EMPTY = -1;
@@ -108,7 +113,31 @@ __device__ __forceinline__ void probe_batch(const int32_t *__restrict__ ci_ik, c
   int o = 0;
   uint32_t o_end = rec.incl[0];
   uint32_t addr = rec.s0[0];  // column of probe q is addr + q (mod 2^32)
-  for (uint32_t qb = lane; qb < total; qb += 32 * U) {
+  uint32_t qb = lane;
+  // full rounds: every lane's U probes exist (the test is warp-uniform)
+  for (; qb - lane + 32u * U <= total; qb += 32u * U) {
+    int32_t wv[U];
+    int own[U];
+    uint32_t qpos[U];
+#pragma unroll
+    for (int r = 0; r < U; ++r) {
+      const uint32_t q = qb + 32u * r;
+      while (q >= o_end) {
+        ++o;
+        const uint32_t prev_end = o_end;
+        o_end = rec.incl[o];
+        addr = rec.s0[o] - prev_end;
+      }
+      qpos[r] = addr + q;
+      wv[r] = ci_ik[qpos[r]];
+      own[r] = o;
+    }
+#pragma unroll
+    for (int r = 0; r < U; ++r)
+      if (lookup(wv[r], own[r])) on_hit(wv[r], own[r], qpos[r]);
+  }
+  // the last, partial round
+  if (qb - lane < total) {
     int32_t wv[U];
     int own[U];
     uint32_t qpos[U];
@@ -270,7 +299,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
             if (blen <= STAGE) mode = ST_SORTED;
           } else if (span <= (int64_t)STAGE * 32) {
             mode = ST_BITMAP;
-          } else if (blen <= STAGE / 2 && (kflag == 1 || blen > hash_min)) {
+          } else if (2 * blen <= STAGE_POW2 && (kflag == 1 || blen > hash_min)) {
             mode = ST_HASH;
           } else if (kflag == 2 && blen <= STAGE) {
             mode = ST_SORTED;
@@ -447,14 +476,29 @@ bbtc_status configure_mode(int *blocks_per_sm) {
 }  // namespace
 
 bbtc_status configure_count_kernels(Plan *pl) {
-  BBTC_TRY(configure_mode<0>(&pl->blocks_per_sm[0]));
-  BBTC_TRY(configure_mode<1>(&pl->blocks_per_sm[1]));
-  BBTC_TRY(configure_mode<2>(&pl->blocks_per_sm[2]));
-  BBTC_TRY(configure_mode<3>(&pl->blocks_per_sm[3]));
-  BBTC_TRY(configure_mode<4>(&pl->blocks_per_sm[4]));
-  BBTC_TRY(configure_mode<5>(&pl->blocks_per_sm[5]));
-  BBTC_TRY(configure_mode<6>(&pl->blocks_per_sm[6]));
-  BBTC_TRY(configure_mode<7>(&pl->blocks_per_sm[7]));
+  // the attributes and occupancies are per device: set and query them once
+  static std::mutex mu;
+  static int cached[64][8];
+  static bool done[64] = {false};
+  int dev = 0;
+  BBTC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range", dev);
+    return BBTC_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done[dev]) {
+    BBTC_TRY(configure_mode<0>(&cached[dev][0]));
+    BBTC_TRY(configure_mode<1>(&cached[dev][1]));
+    BBTC_TRY(configure_mode<2>(&cached[dev][2]));
+    BBTC_TRY(configure_mode<3>(&cached[dev][3]));
+    BBTC_TRY(configure_mode<4>(&cached[dev][4]));
+    BBTC_TRY(configure_mode<5>(&cached[dev][5]));
+    BBTC_TRY(configure_mode<6>(&cached[dev][6]));
+    BBTC_TRY(configure_mode<7>(&cached[dev][7]));
+    done[dev] = true;
+  }
+  for (int i = 0; i < 8; ++i) pl->blocks_per_sm[i] = cached[dev][i];
   return BBTC_OK;
 }
 

@@ -38,23 +38,18 @@ __global__ void k_cuts(const int64_t *__restrict__ rowptr, int64_t n, int p,
 
 // In-edges of part a (the edges of rows V_a, positions [rowptr[c_a],
 // rowptr[c_a+1]) of the oriented CSR) grouped by destination v: a counting
-// sort on v - c_a. Step 1 counts the edges into each v (warp-aggregated:
-// lanes with equal v add once).
+// sort on v - c_a. Step 1 counts the edges into each v. (A warp's 32
+// consecutive edges span about two rows, whose destinations are distinct, so
+// aggregating equal keys within the warp would save little.)
 __global__ void k_inedge_count(const int64_t *__restrict__ rowptr,
                                const int32_t *__restrict__ colidx,
                                const int32_t *__restrict__ cuts, int a,
                                unsigned long long *__restrict__ hist) {
   const int32_t c_a = cuts[a];
   const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
-  const unsigned lane = threadIdx.x & 31u;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = e0 + (int64_t)blockIdx.x * blockDim.x; base < e1; base += stride) {
-    const int64_t e = base + threadIdx.x;
-    const int32_t key = e < e1 ? colidx[e] - c_a : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    if (key >= 0 && lane == (unsigned)(__ffs(peers) - 1))
-      atomicAdd(&hist[key], (unsigned long long)__popc(peers));
-  }
+  for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
+       e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&hist[colidx[e] - c_a], 1ull);
 }
 
 // Step 2 (after an exclusive scan of the counts): the block offsets of part a,
@@ -77,35 +72,36 @@ __global__ void k_inedge_offsets(const int64_t *__restrict__ rowptr,
   boff[a * (p + 1) + j] = off;
 }
 
-// Step 3: scatter each edge of part a to its destination's run; within a run
-// the order of the sources is whatever the atomics give (counts do not depend
-// on it).
+// Step 3: scatter each edge of part a to its destination's run, as one
+// 16-byte record (source, destination, block position) so that each random
+// write touches one sector; within a run the order of the sources is whatever
+// the atomics give (counts do not depend on it).
 __global__ void k_inedge_scatter(const int64_t *__restrict__ rowptr,
                                  const int32_t *__restrict__ colidx,
                                  const int32_t *__restrict__ esrc,
                                  const uint32_t *__restrict__ pos_of_edge,
                                  const int32_t *__restrict__ cuts, int a,
-                                 unsigned long long *__restrict__ offs,
-                                 int32_t *__restrict__ ie_u, int32_t *__restrict__ ie_v,
-                                 uint32_t *__restrict__ ie_e) {
+                                 unsigned long long *__restrict__ offs, int4 *__restrict__ rec) {
   const int32_t c_a = cuts[a];
   const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
-  const unsigned lane = threadIdx.x & 31u;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = e0 + (int64_t)blockIdx.x * blockDim.x; base < e1; base += stride) {
-    const int64_t e = base + threadIdx.x;
-    const int32_t key = e < e1 ? colidx[e] - c_a : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int leader = __ffs(peers) - 1;
-    unsigned long long b = 0;
-    if (key >= 0 && (int)lane == leader) b = atomicAdd(&offs[key], (unsigned long long)__popc(peers));
-    b = __shfl_sync(0xffffffffu, b, leader);
-    if (key >= 0) {
-      const int64_t x = e0 + (int64_t)b + __popc(peers & ((1u << lane) - 1u));
-      ie_u[x] = esrc[e];
-      ie_v[x] = key + c_a;
-      ie_e[x] = pos_of_edge[e];
-    }
+  for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t key = colidx[e] - c_a;
+    const int64_t x = e0 + (int64_t)atomicAdd(&offs[key], 1ull);
+    rec[x] = make_int4(esrc[e], key + c_a, (int32_t)pos_of_edge[e], 0);
+  }
+}
+
+// Step 4 (all parts): the records, now in in-edge order, to the three arrays.
+__global__ void k_inedge_unpack(const int4 *__restrict__ rec, int64_t m,
+                                int32_t *__restrict__ ie_u, int32_t *__restrict__ ie_v,
+                                uint32_t *__restrict__ ie_e) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int4 r = rec[x];
+    ie_u[x] = r.x;
+    ie_v[x] = r.y;
+    ie_e[x] = (uint32_t)r.z;
   }
 }
 
@@ -401,7 +397,9 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   PLAN_TRY(dalloc_n(&pl.boff, (int64_t)p * (p + 1), s));
   {
     unsigned long long *hist = nullptr;
+    int4 *rec = nullptr;
     PLAN_TRY(scratch.get(&hist, n + 1));
+    PLAN_TRY(scratch.get(&rec, m > 0 ? m : 1));
     for (int a = 0; a < p; ++a) {
       const int64_t bins = n - pl.h_cuts[a];
       if (cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (size_t)(bins + 1), s) !=
@@ -423,10 +421,13 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
       PLAN_TRY(launch_status("build_plan"));
       if (m > 0) {
         k_inedge_scatter<<<grid_for(part_edges_hint, 256, 32), 256, 0, s>>>(
-            g->rowptr, g->colidx, g->esrc, pos_of_edge, pl.cuts, a, hist, pl.ie_u, pl.ie_v,
-            pl.ie_e);
+            g->rowptr, g->colidx, g->esrc, pos_of_edge, pl.cuts, a, hist, rec);
         PLAN_TRY(launch_status("build_plan"));
       }
+    }
+    if (m > 0) {
+      k_inedge_unpack<<<grid_for(m, 256, 32), 256, 0, s>>>(rec, m, pl.ie_u, pl.ie_v, pl.ie_e);
+      PLAN_TRY(launch_status("build_plan"));
     }
   }
 
