@@ -564,6 +564,24 @@ def main():
         if len(totals) != 1:
             raise SystemExit(f"inconsistent triangle counts across steps: {sorted(totals)}")
 
+        # pinned host-to-device bandwidth right now (streamed counts depend on it,
+        # and it varies from box to box)
+        h2d_gbs = None
+        if budget:
+            k = min(int(h_ci.numel()), 1 << 28)
+            tmp = torch.empty(k, dtype=torch.int32, device="cuda")
+            with torch.cuda.stream(stream):
+                tmp.copy_(h_ci[:k], non_blocking=True)
+                b0 = torch.cuda.Event(enable_timing=True)
+                b1 = torch.cuda.Event(enable_timing=True)
+                b0.record(stream)
+                for _ in range(3):
+                    tmp.copy_(h_ci[:k], non_blocking=True)
+                b1.record(stream)
+            torch.cuda.synchronize()
+            h2d_gbs = 3 * 4 * k / (b0.elapsed_time(b1) / 1000.0) / 1e9
+            del tmp
+
         if rank == 0:
             peak, peak_kind = measured_peaks()
             kms = sum(count_ms) / len(count_ms)
@@ -594,7 +612,7 @@ def main():
                     "phase_ms": {"prep": statistics.mean(prep_ms), "plan": statistics.mean(plan_ms),
                                  "count_kernel": kms},
                     "device_budget_gb": budget_gb,
-                    "streaming": stream_info[-1] if budget else None,
+                    "streaming": dict(stream_info[-1], pinned_h2d_gbs=h2d_gbs) if budget else None,
                 },
                 "e2e": {"value": replica_throughput(m, world, e2e_ms), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},

@@ -410,13 +410,9 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   if (task_cycles)
     BBTC_CUDA(cudaMemcpyAsync(opts.per_task_cycles_out, task_cycles,
                               sizeof(uint64_t) * (size_t)pl.ntasks, kind, s));
-  if (edge_sup && g->m > 0) {
-    unsigned *by_csr = nullptr;
-    BBTC_TRY(scratch.get(&by_csr, g->m));
-    BBTC_TRY(edge_support_to_csr(g, pl, edge_sup, by_csr, s));
-    BBTC_CUDA(cudaMemcpyAsync(opts.per_edge_out, by_csr, sizeof(uint32_t) * (size_t)g->m, kind,
+  if (edge_sup && g->m > 0)  // resident plans index the oriented CSR directly
+    BBTC_CUDA(cudaMemcpyAsync(opts.per_edge_out, edge_sup, sizeof(uint32_t) * (size_t)g->m, kind,
                               s));
-  }
   if (opts.per_vertex_out && g->n > 0) {
     unsigned long long *by_id = nullptr;
     BBTC_TRY(scratch.get(&by_id, g->n));

@@ -103,13 +103,13 @@ struct LaneRec {
 // the lane-record o whose inclusive prefix first exceeds q and reads column
 // rec.s0[o] + q - (prefix before o). Lane l takes q = l, l + 32, ...; U probes
 // per lane per round have their loads issued before any lookup, so each lane
-// keeps U global loads in flight. Column indices are local to the block
-// arrays and below 2^32.
-template <typename OnHit, typename Lookup>
+// keeps U global loads in flight (4 suits the one-load lookups; the halving
+// searches, which keep more registers live, take 3). Column indices are local
+// to the block arrays and below 2^32.
+template <int U, typename OnHit, typename Lookup>
 __device__ __forceinline__ void probe_batch(const int32_t *__restrict__ ci_ik, const LaneRec &rec,
                                             uint32_t total, unsigned lane, OnHit &on_hit,
                                             Lookup lookup) {
-  constexpr int U = 4;
   int o = 0;
   uint32_t o_end = rec.incl[0];
   uint32_t addr = rec.s0[0];  // column of probe q is addr + q (mod 2^32)
@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
     const int32_t *__restrict__ ci_ik = d.ci_ik;
     const int32_t *__restrict__ ci_jk = d.ci_jk;
     const int64_t ik_off = d.ci_ik_off, jk_off = d.ci_jk_off;
+    const int64_t rs_ik = d.rs_ik, rs_jk = d.rs_jk;
     const int32_t c_i = d.c_i, c_j = d.c_j;
     const bool diag = d.diag != 0;
     unsigned long long acc = 0;
@@ -248,21 +249,21 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
       int64_t b0 = 0, b1 = 0;
       if (uniform) {
         if (lane == 0) {
-          b0 = (int64_t)rp_jk[v0 - c_j] - jk_off;
-          b1 = (int64_t)rp_jk[v0 - c_j + 1] - jk_off;
+          b0 = (int64_t)rp_jk[(v0 - c_j) * rs_jk] - jk_off;
+          b1 = (int64_t)rp_jk[(v0 - c_j) * rs_jk + 1] - jk_off;
         }
         b0 = __shfl_sync(0xffffffffu, b0, 0);
         b1 = __shfl_sync(0xffffffffu, b1, 0);
       } else if (active) {
-        b0 = (int64_t)rp_jk[v - c_j] - jk_off;
-        b1 = (int64_t)rp_jk[v - c_j + 1] - jk_off;
+        b0 = (int64_t)rp_jk[(v - c_j) * rs_jk] - jk_off;
+        b1 = (int64_t)rp_jk[(v - c_j) * rs_jk + 1] - jk_off;
       }
       // N(G_ik, u) restricted to entries above v (for k == j, the entries of
       // G_ij after (u, v) itself); [s0, s1) local to ci_ik
       int64_t s0 = 0, s1 = 0;
       if (active && b1 > b0) {
-        s1 = (int64_t)rp_ik[u - c_i + 1] - ik_off;
-        s0 = diag ? e + 1 - ik_off : (int64_t)rp_ik[u - c_i] - ik_off;
+        s1 = (int64_t)rp_ik[(u - c_i) * rs_ik + 1] - ik_off;
+        s0 = diag ? e + 1 - ik_off : (int64_t)rp_ik[(u - c_i) * rs_ik] - ik_off;
       }
       const uint32_t len = (uint32_t)(s1 - s0);
       const uint32_t incl = warp_inclusive_scan(len);
@@ -393,20 +394,23 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         const unsigned *__restrict__ bm = reinterpret_cast<const unsigned *>(stage);
         const int32_t first = staged_first;
         const uint32_t span = (uint32_t)staged_len;
-        probe_batch(ci_ik, rec, total, lane, on_hit, [&](int32_t w, int) {
+        probe_batch<4>(ci_ik, rec, total, lane, on_hit, [&](int32_t w, int) {
+          // branch-free: the word index is clamped into the bitmap, and the
+          // range test masks the bit
           const uint32_t dlt = (uint32_t)(w - first);
-          return dlt < span && ((bm[dlt >> 5] >> (dlt & 31u)) & 1u);
+          const uint32_t word = bm[min(dlt >> 5, (uint32_t)(STAGE - 1))];
+          return ((dlt < span) & (word >> (dlt & 31u))) & 1u;
         });
       } else if (staged && staged_mode == ST_HASH) {
         const int log2h = staged_log2h;
-        probe_batch(ci_ik, rec, total, lane, on_hit,
-                    [&](int32_t w, int) { return hash_contains(stage, log2h, w); });
+        probe_batch<4>(ci_ik, rec, total, lane, on_hit,
+                       [&](int32_t w, int) { return hash_contains(stage, log2h, w); });
       } else if (staged) {
         const int slen = staged_len;
-        probe_batch(ci_ik, rec, total, lane, on_hit,
-                    [&](int32_t w, int) { return sorted_contains(stage, slen, w); });
+        probe_batch<3>(ci_ik, rec, total, lane, on_hit,
+                       [&](int32_t w, int) { return sorted_contains(stage, slen, w); });
       } else {
-        probe_batch(ci_ik, rec, total, lane, on_hit, [&](int32_t w, int o) {
+        probe_batch<3>(ci_ik, rec, total, lane, on_hit, [&](int32_t w, int o) {
           const int64_t lo = uniform ? b0 : rec.b0[o];
           const int64_t hi = uniform ? b1 : rec.b1[o];
           const int64_t pos = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, w);

@@ -7,12 +7,17 @@ namespace bbtc {
 
 // Where the counting kernel finds the three blocks of task t = (i, j, k):
 //  - the in-edges of G_ij (source u, destination v, position of (u,v) among
-//    G_ij's columns), grouped by v: element x of the task's range lives at
+//    the columns), grouped by v: element x of the task's range lives at
 //    ie_*[x - ie_off];
-//  - N(G_ik, u) for u in V_i: columns [rp_ik[u - c_i], rp_ik[u - c_i + 1]) of
-//    ci_ik, where column position q lives at ci_ik[q - ci_ik_off];
-//  - N(G_jk, v) for v in V_j: likewise through rp_jk / ci_jk.
-// For k == j, G_ik is G_ij and the in-edge position indexes it directly.
+//  - N(G_ik, u) for u in V_i: columns [rp_ik[r * rs_ik], rp_ik[r * rs_ik + 1])
+//    with r = u - c_i, of ci_ik, where column position q lives at
+//    ci_ik[q - ci_ik_off];
+//  - N(G_jk, v) for v in V_j: likewise through rp_jk / rs_jk / ci_jk.
+// Resident plans point into the oriented CSR itself: rp is the split table
+// (row r of part a holds the CSR positions where its runs in blocks a..p-1
+// start, then its end; rs = p - a + 1). Streamed plans point at physical
+// per-block copies (rs = 1). For k == j, G_ik is G_ij and the in-edge
+// position indexes it directly.
 struct TaskDesc {
   const int32_t *ie_u;
   const int32_t *ie_v;
@@ -24,6 +29,7 @@ struct TaskDesc {
   const uint32_t *rp_jk;
   const int32_t *ci_jk;
   int64_t ci_jk_off;
+  int32_t rs_ik, rs_jk;
   int32_t c_i, c_j;
   int32_t diag;  // k == j
   int32_t task;  // index in Alg. 4 order
@@ -44,17 +50,24 @@ struct Plan {
   int64_t ntasks = 0;
   int32_t *cuts = nullptr;      // p+1
   int32_t h_cuts[65] = {0};     // host copy of the cuts
-  // physical block CSR (Sec. 4.1, BCSR): blocks (a, b), a <= b, in row-major
-  // order; block (a, b)'s row pointers are rp[rpb[a*p+b] .. + |V_a|] and hold
-  // positions in ci, the block-major concatenation of all blocks' columns
+  // blocks G_ab of the resident plan, read in place from the oriented CSR
+  // (Sec. 4.1, the blocks of a row are consecutive runs of its sorted list):
+  // spl[h_spl_off[a] + r * (p - a + 1) + (b - a)] = CSR position where row
+  // c_a + r enters block b (b = p: the row's end)
+  uint32_t *spl = nullptr;
+  int64_t h_spl_off[65] = {0};
+  // physical block CSR (streamed plans only): blocks (a, b), a <= b, in
+  // row-major order; block (a, b)'s row pointers are rp[rpb[a*p+b] .. + |V_a|]
+  // and hold positions in ci, the block-major concatenation of all blocks'
+  // columns; in-edge positions then index ci
   uint32_t *rp = nullptr;
   int32_t *ci = nullptr;
   int64_t h_rpb[64 * 64] = {0};
   int64_t total_rp = 0;
   TaskDesc *desc = nullptr;     // T, in Alg. 4 order
-  int32_t *ie_u = nullptr;      // m: in-edges sorted by (part(u), v, u): source u
+  int32_t *ie_u = nullptr;      // m: in-edges grouped by (part(u), v): source u
   int32_t *ie_v = nullptr;      // m: destination v
-  uint32_t *ie_e = nullptr;     // m: position of the edge (u,v) in ci
+  uint32_t *ie_e = nullptr;     // m: position of the edge (u,v) in the columns
   int64_t *boff = nullptr;      // p*(p+1): block (i,j) in-edges = [boff[i*(p+1)+j], +1)
   int32_t *tasks = nullptr;     // 3*T: (i,j,k) in Alg. 4 order
   double *est = nullptr;        // T: ExecTime in Alg. 4 order
@@ -140,8 +153,9 @@ bbtc_status configure_count_kernels(Plan *pl);
 
 // a9-a10: per-task counts (plan scratch, Alg. 4 order), optional per-vertex
 // counts by position (vertex_count, device, n), per-graph counts (plan
-// scratch) and per-edge support by position in pl.ci (edge_sup, device, m,
-// zeroed by the caller); the total goes to the plan scratch. Enqueues only.
+// scratch) and per-edge support by column position (edge_sup, device, m,
+// zeroed by the caller; resident plans index the oriented CSR, so this is the
+// order of g->colidx); the total goes to the plan scratch. Enqueues only.
 bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                       bool per_graph, uint32_t timeout_ms, cudaStream_t s,
                       cudaEvent_t ev_begin, cudaEvent_t ev_end,
@@ -162,10 +176,10 @@ bbtc_status count_finish(const Plan &pl, cudaStream_t s);
 bbtc_status count_plans(bbtc_graph *const *gs, int32_t ng, uint32_t timeout_ms, cudaStream_t s,
                         uint64_t *counts);
 
-// Per-edge support from block-column order (pl.ci positions) to the order of
-// the oriented CSR's colidx (device arrays of g->m entries; resident plan).
-bbtc_status edge_support_to_csr(const bbtc_graph *g, const Plan &pl, const unsigned *by_block,
-                                unsigned *by_csr, cudaStream_t s);
+// Physical per-block copies of a resident plan's blocks (pl.rp, pl.ci,
+// pl.h_rpb), with the in-edge positions re-pointed at them; the step before a
+// plan streams. Frees the split table.
+bbtc_status plan_physical_blocks(const bbtc_graph *g, Plan &pl, cudaStream_t s);
 
 // a11: count with the blocks streamed from pinned host memory through a
 // device pool of `budget` bytes (two halves, double-buffered).

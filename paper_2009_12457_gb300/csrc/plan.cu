@@ -38,18 +38,43 @@ __global__ void k_cuts(const int64_t *__restrict__ rowptr, int64_t n, int p,
 
 // In-edges of part a (the edges of rows V_a, positions [rowptr[c_a],
 // rowptr[c_a+1]) of the oriented CSR) grouped by destination v: a counting
-// sort on v - c_a. Step 1 counts the edges into each v. (A warp's 32
-// consecutive edges span about two rows, whose destinations are distinct, so
-// aggregating equal keys within the warp would save little.)
-__global__ void k_inedge_count(const int64_t *__restrict__ rowptr,
-                               const int32_t *__restrict__ colidx,
-                               const int32_t *__restrict__ cuts, int a,
-                               unsigned long long *__restrict__ hist) {
+// sort on v - c_a. In degree order the hubs hold the top positions and
+// receive most in-edges (on R-MAT, the top 8192 of 2 M vertices receive 65%),
+// so one global counter per hub would serialise. Each CTA takes a contiguous
+// share of the part's edges and counts destinations in the top IE_HUB
+// positions in shared memory, adding to the global counters once per CTA.
+constexpr int IE_NT = 256;
+constexpr int IE_NT_S = 512;  // scatter CTAs: more threads to keep position atomics in flight
+constexpr int IE_HUB = 8192;
+
+__device__ __forceinline__ void ie_share(int64_t e0, int64_t e1, int64_t *b0, int64_t *b1) {
+  const int64_t per = (e1 - e0 + gridDim.x - 1) / gridDim.x;
+  *b0 = e0 + (int64_t)blockIdx.x * per;
+  *b1 = *b0 + per < e1 ? *b0 + per : e1;
+}
+
+// Step 1: count the edges into each destination.
+__global__ void __launch_bounds__(IE_NT) k_inedge_count(const int64_t *__restrict__ rowptr,
+                                                        const int32_t *__restrict__ colidx,
+                                                        const int32_t *__restrict__ cuts, int a,
+                                                        int64_t n,
+                                                        unsigned long long *__restrict__ hist) {
+  __shared__ unsigned sm[IE_HUB];
   const int32_t c_a = cuts[a];
   const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
-  for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
-       e += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&hist[colidx[e] - c_a], 1ull);
+  const int64_t hub0 = n - IE_HUB > c_a ? n - IE_HUB : c_a;  // positions >= hub0 on chip
+  for (int i = threadIdx.x; i < IE_HUB; i += IE_NT) sm[i] = 0;
+  __syncthreads();
+  int64_t b0, b1;
+  ie_share(e0, e1, &b0, &b1);
+  for (int64_t e = b0 + threadIdx.x; e < b1; e += IE_NT) {
+    const int32_t v = colidx[e];
+    if (v >= hub0) atomicAdd(&sm[v - hub0], 1u);
+    else atomicAdd(&hist[v - c_a], 1ull);
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n - hub0; i += IE_NT)
+    if (sm[i]) atomicAdd(&hist[hub0 - c_a + i], (unsigned long long)sm[i]);
 }
 
 // Step 2 (after an exclusive scan of the counts): the block offsets of part a,
@@ -73,22 +98,56 @@ __global__ void k_inedge_offsets(const int64_t *__restrict__ rowptr,
 }
 
 // Step 3: scatter each edge of part a to its destination's run, as one
-// 16-byte record (source, destination, block position) so that each random
+// 16-byte record (source, destination, CSR position) so that each random
 // write touches one sector; within a run the order of the sources is whatever
-// the atomics give (counts do not depend on it).
-__global__ void k_inedge_scatter(const int64_t *__restrict__ rowptr,
-                                 const int32_t *__restrict__ colidx,
-                                 const int32_t *__restrict__ esrc,
-                                 const uint32_t *__restrict__ pos_of_edge,
-                                 const int32_t *__restrict__ cuts, int a,
-                                 unsigned long long *__restrict__ offs, int4 *__restrict__ rec) {
+// the atomics give (counts do not depend on it). For hub destinations the CTA
+// first counts its share, reserves one range per hub with a single global
+// atomic, and hands out positions inside it from shared memory.
+__global__ void __launch_bounds__(IE_NT_S) k_inedge_scatter(const int64_t *__restrict__ rowptr,
+                                                            const int32_t *__restrict__ colidx,
+                                                            const int32_t *__restrict__ esrc,
+                                                            const int32_t *__restrict__ cuts, int a,
+                                                            int64_t n,
+                                                            unsigned long long *__restrict__ offs,
+                                                            int4 *__restrict__ rec) {
+  __shared__ unsigned sm[IE_HUB];
   const int32_t c_a = cuts[a];
   const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
-  for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t key = colidx[e] - c_a;
-    const int64_t x = e0 + (int64_t)atomicAdd(&offs[key], 1ull);
-    rec[x] = make_int4(esrc[e], key + c_a, (int32_t)pos_of_edge[e], 0);
+  const int64_t hub0 = n - IE_HUB > c_a ? n - IE_HUB : c_a;
+  for (int i = threadIdx.x; i < IE_HUB; i += IE_NT_S) sm[i] = 0;
+  __syncthreads();
+  int64_t b0, b1;
+  ie_share(e0, e1, &b0, &b1);
+  for (int64_t e = b0 + threadIdx.x; e < b1; e += IE_NT_S) {
+    const int32_t v = colidx[e];
+    if (v >= hub0) atomicAdd(&sm[v - hub0], 1u);
+  }
+  __syncthreads();
+  // positions are relative to e0 and below 2^32
+  for (int64_t i = threadIdx.x; i < n - hub0; i += IE_NT_S)
+    if (sm[i]) sm[i] = (unsigned)atomicAdd(&offs[hub0 - c_a + i], (unsigned long long)sm[i]);
+  __syncthreads();
+  // IE_ILP edges per thread per step: their position atomics are in flight together
+  constexpr int IE_ILP = 4;
+  for (int64_t e = b0 + threadIdx.x; e < b1; e += (int64_t)IE_NT_S * IE_ILP) {
+    int32_t v[IE_ILP];
+    uint64_t x[IE_ILP];
+#pragma unroll
+    for (int r = 0; r < IE_ILP; ++r) {
+      const int64_t idx = e + (int64_t)r * IE_NT_S;
+      v[r] = idx < b1 ? colidx[idx] : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < IE_ILP; ++r)
+      if (v[r] >= 0)
+        x[r] = v[r] >= hub0 ? (uint64_t)atomicAdd(&sm[v[r] - hub0], 1u)
+                            : (uint64_t)atomicAdd(&offs[v[r] - c_a], 1ull);
+#pragma unroll
+    for (int r = 0; r < IE_ILP; ++r) {
+      const int64_t idx = e + (int64_t)r * IE_NT_S;
+      if (v[r] >= 0)
+        rec[e0 + (int64_t)x[r]] = make_int4(esrc[idx], v[r], (int32_t)(uint32_t)idx, 0);
+    }
   }
 }
 
@@ -103,6 +162,42 @@ __global__ void k_inedge_unpack(const int4 *__restrict__ rec, int64_t m,
     ie_v[x] = r.y;
     ie_e[x] = (uint32_t)r.z;
   }
+}
+
+// The split table of the resident blocks: for row u of part a (sorted,
+// every entry above u, so in blocks a..p-1), the CSR positions where its runs
+// in blocks a, a+1, ..., p-1 start, then its end.
+__global__ void k_splits(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                         int64_t n, const int32_t *__restrict__ cuts_g, int p,
+                         const int64_t *__restrict__ off_g, uint32_t *__restrict__ spl) {
+  __shared__ int32_t cuts[MAXP + 1];
+  __shared__ int64_t off[MAXP + 1];
+  for (int i = threadIdx.x; i <= p; i += blockDim.x) {
+    cuts[i] = cuts_g[i];
+    off[i] = off_g[i];
+  }
+  __syncthreads();
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int a = part_of_dev(cuts, p, (int32_t)u);
+    const int64_t r0 = rowptr[u], r1 = rowptr[u + 1];
+    uint32_t *row = spl + off[a] + (u - cuts[a]) * (int64_t)(p - a + 1);
+    row[0] = (uint32_t)r0;
+    int64_t lo = r0;
+    for (int b = a + 1; b < p; ++b) {
+      lo = lower_bound_dev<int32_t, int64_t>(colidx, lo, r1, cuts[b]);
+      row[b - a] = (uint32_t)lo;
+    }
+    row[p - a] = (uint32_t)r1;
+  }
+}
+
+// In-edge positions from CSR positions to physical block positions.
+__global__ void k_remap_positions(uint32_t *__restrict__ ie_e, int64_t m,
+                                  const uint32_t *__restrict__ pos_of_edge) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m;
+       x += (int64_t)gridDim.x * blockDim.x)
+    ie_e[x] = pos_of_edge[ie_e[x]];
 }
 
 // BCSR, step 1 (one thread per oriented edge e = (u, v)): the edge falls in
@@ -259,29 +354,6 @@ __global__ void k_item_fill(const int32_t *__restrict__ order, const int32_t *__
   }
 }
 
-// Per-edge values from block-column order to oriented-CSR order: oriented
-// edge e = (u, v) sits in block (part(u), part(v)) at the run of row u that
-// starts at the first entry of the row at or above c_part(v).
-__global__ void k_edge_to_csr(const int32_t *__restrict__ esrc, const int32_t *__restrict__ colidx,
-                              const int64_t *__restrict__ rowptr, int64_t m,
-                              const int32_t *__restrict__ cuts_g, int p,
-                              const int64_t *__restrict__ rpb_g, const uint32_t *__restrict__ rp,
-                              const unsigned *__restrict__ by_block, unsigned *__restrict__ by_csr) {
-  __shared__ int32_t cuts[MAXP + 1];
-  __shared__ int64_t rpb[MAXP * MAXP];
-  for (int i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
-  for (int i = threadIdx.x; i < p * p; i += blockDim.x) rpb[i] = rpb_g[i];
-  __syncthreads();
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = esrc[e], v = colidx[e];
-    const int a = part_of_dev(cuts, p, u), b = part_of_dev(cuts, p, v);
-    const int64_t run0 = lower_bound_dev<int32_t, int64_t>(colidx, rowptr[u], rowptr[u + 1], cuts[b]);
-    const int64_t slot = rpb[a * p + b] + (u - cuts[a]);
-    by_csr[e] = by_block[(int64_t)rp[slot] + (e - run0)];
-  }
-}
-
 }  // namespace
 
 void free_plan(Plan *pl, cudaStream_t s) {
@@ -297,6 +369,7 @@ void free_plan(Plan *pl, cudaStream_t s) {
   dfree(pl->scratch, s);
   dfree(pl->rp, s);
   dfree(pl->ci, s);
+  dfree(pl->spl, s);
   dfree(pl->desc, s);
   free_plan_host(pl);
   *pl = Plan();
@@ -340,8 +413,8 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   k_cuts<<<1, MAXP + 1, 0, s>>>(g->rowptr, n, p, pl.cuts);
   PLAN_TRY(launch_status("build_plan"));
 
-  // a6: physical blocks. Host table of blocks (a, b), a <= b, row-major, each
-  // with a row-pointer segment of |V_a| + 1 slots.
+  // a6: the blocks, read in place from the oriented CSR through the split
+  // table (per part a: |V_a| rows of p - a + 1 positions)
   if (cudaMemcpyAsync(pl.h_cuts, pl.cuts, sizeof(int32_t) * (size_t)(p + 1),
                       cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
@@ -351,43 +424,26 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   }
   {
     int64_t off = 0;
-    for (int a = 0; a < p; ++a)
-      for (int b = a; b < p; ++b) {
-        pl.h_rpb[a * p + b] = off;
-        off += (int64_t)(pl.h_cuts[a + 1] - pl.h_cuts[a]) + 1;
-      }
-    pl.total_rp = off;
+    for (int a = 0; a < p; ++a) {
+      pl.h_spl_off[a] = off;
+      off += (int64_t)(pl.h_cuts[a + 1] - pl.h_cuts[a]) * (p - a + 1);
+    }
+    pl.h_spl_off[p] = off;
   }
-  int64_t *d_rpb = nullptr;
-  uint64_t *cnt = nullptr;
-  uint32_t *start = nullptr, *pos_of_edge = nullptr;
-  PLAN_TRY(scratch.get(&d_rpb, (int64_t)p * p));
-  PLAN_TRY(scratch.get(&cnt, pl.total_rp));
-  PLAN_TRY(scratch.get(&start, pl.total_rp));
-  PLAN_TRY(scratch.get(&pos_of_edge, m));
-  PLAN_TRY(dalloc_n(&pl.rp, pl.total_rp, s));
-  PLAN_TRY(dalloc_n(&pl.ci, m, s));
-  if (cudaMemcpyAsync(d_rpb, pl.h_rpb, sizeof(int64_t) * (size_t)p * p, cudaMemcpyHostToDevice,
-                      s) != cudaSuccess ||
-      cudaMemsetAsync(cnt, 0, sizeof(uint64_t) * (size_t)pl.total_rp, s) != cudaSuccess) {
-    set_error("build_plan: copying the block table failed");
+  int64_t *d_spl_off = nullptr;
+  PLAN_TRY(scratch.get(&d_spl_off, p + 1));
+  PLAN_TRY(dalloc_n(&pl.spl, pl.h_spl_off[p] > 0 ? pl.h_spl_off[p] : 1, s));
+  if (cudaMemcpyAsync(d_spl_off, pl.h_spl_off, sizeof(int64_t) * (size_t)(p + 1),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    set_error("build_plan: copying the split offsets failed");
     free_plan(&pl, s);
     return BBTC_ECUDA;
   }
-  if (m > 0) {
-    k_bcsr_count<<<grid_for(m, 256, 32), 256, 0, s>>>(
-        g->esrc, g->colidx, m, pl.cuts, p, d_rpb,
-        reinterpret_cast<unsigned long long *>(cnt), start);
+  if (n > 0) {
+    k_splits<<<grid_for(n, 256, 16), 256, 0, s>>>(g->rowptr, g->colidx, n, pl.cuts, p, d_spl_off,
+                                                  pl.spl);
     PLAN_TRY(launch_status("build_plan"));
   }
-  PLAN_TRY(exclusive_scan_u64(cnt, cnt, pl.total_rp, s));
-  if (m > 0) {
-    k_bcsr_fill<<<grid_for(m, 256, 32), 256, 0, s>>>(g->esrc, g->colidx, m, pl.cuts, p, d_rpb,
-                                                     cnt, start, pl.ci, pos_of_edge);
-    PLAN_TRY(launch_status("build_plan"));
-  }
-  k_bcsr_rowptr<<<grid_for(pl.total_rp, 256, 32), 256, 0, s>>>(cnt, pl.total_rp, pl.rp);
-  PLAN_TRY(launch_status("build_plan"));
 
   // in-edges grouped by (part(u), v), and the block offsets: one counting
   // sort on the destination per part
@@ -408,10 +464,10 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
         free_plan(&pl, s);
         return BBTC_ECUDA;
       }
-      const int64_t part_edges_hint = m / p + 1;
+      // a few CTAs per SM, each with a contiguous share of the part's edges
+      const unsigned ie_grid = grid_for(m / p + 1, IE_NT * 64, 4);
       if (m > 0) {
-        k_inedge_count<<<grid_for(part_edges_hint, 256, 32), 256, 0, s>>>(g->rowptr, g->colidx,
-                                                                        pl.cuts, a, hist);
+        k_inedge_count<<<ie_grid, IE_NT, 0, s>>>(g->rowptr, g->colidx, pl.cuts, a, n, hist);
         PLAN_TRY(launch_status("build_plan"));
       }
       if (bins > 0)
@@ -420,8 +476,8 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
       k_inedge_offsets<<<1, MAXP + 1, 0, s>>>(g->rowptr, pl.cuts, a, p, hist, bins, pl.boff);
       PLAN_TRY(launch_status("build_plan"));
       if (m > 0) {
-        k_inedge_scatter<<<grid_for(part_edges_hint, 256, 32), 256, 0, s>>>(
-            g->rowptr, g->colidx, g->esrc, pos_of_edge, pl.cuts, a, hist, rec);
+        k_inedge_scatter<<<ie_grid, IE_NT_S, 0, s>>>(g->rowptr, g->colidx, g->esrc, pl.cuts, a,
+                                                      n, hist, rec);
         PLAN_TRY(launch_status("build_plan"));
       }
     }
@@ -467,11 +523,13 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
           d.ie_v = pl.ie_v;
           d.ie_e = pl.ie_e;
           d.ie_off = 0;
-          d.rp_ik = pl.rp + pl.h_rpb[i * p + k];
-          d.ci_ik = pl.ci;
+          d.rp_ik = pl.spl + pl.h_spl_off[i] + (k - i);
+          d.rs_ik = p - i + 1;
+          d.ci_ik = g->colidx;
           d.ci_ik_off = 0;
-          d.rp_jk = pl.rp + pl.h_rpb[j * p + k];
-          d.ci_jk = pl.ci;
+          d.rp_jk = pl.spl + pl.h_spl_off[j] + (k - j);
+          d.rs_jk = p - j + 1;
+          d.ci_jk = g->colidx;
           d.ci_jk_off = 0;
           d.c_i = pl.h_cuts[i];
           d.c_j = pl.h_cuts[j];
@@ -523,29 +581,56 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   PLAN_TRY(dalloc_n(&pl.scratch, SCR_TASKS + nt + g->ng, s));
   PLAN_TRY(configure_count_kernels(&pl));
 #undef PLAN_TRY
-  pl.bytes = (uint64_t)m * 16 + (uint64_t)pl.total_rp * 4 + (uint64_t)nt * (24 + sizeof(TaskDesc)) +
+  pl.bytes = (uint64_t)m * 12 + (uint64_t)pl.h_spl_off[p] * 4 + (uint64_t)nt * (24 + sizeof(TaskDesc)) +
              (uint64_t)pl.nitems * sizeof(WorkItem) + (uint64_t)(SCR_TASKS + nt + g->ng) * 8;
   g->plan = pl;
   return BBTC_OK;
 }
 
-bbtc_status edge_support_to_csr(const bbtc_graph *g, const Plan &pl, const unsigned *by_block,
-                                unsigned *by_csr, cudaStream_t s) {
-  if (pl.streamed || !pl.rp) {
-    set_error("internal: per-edge support needs a resident plan");
-    return BBTC_EINTERNAL;
-  }
-  if (g->m == 0) return BBTC_OK;
+bbtc_status plan_physical_blocks(const bbtc_graph *g, Plan &pl, cudaStream_t s) {
+  if (pl.rp) return BBTC_OK;
   const int p = pl.p;
+  const int64_t m = g->m;
+  {
+    int64_t off = 0;
+    for (int a = 0; a < p; ++a)
+      for (int b = a; b < p; ++b) {
+        pl.h_rpb[a * p + b] = off;
+        off += (int64_t)(pl.h_cuts[a + 1] - pl.h_cuts[a]) + 1;
+      }
+    pl.total_rp = off;
+  }
   Scratch scratch(s);
   int64_t *d_rpb = nullptr;
+  uint64_t *cnt = nullptr;
+  uint32_t *start = nullptr, *pos_of_edge = nullptr;
   BBTC_TRY(scratch.get(&d_rpb, (int64_t)p * p));
+  BBTC_TRY(scratch.get(&cnt, pl.total_rp));
+  BBTC_TRY(scratch.get(&start, pl.total_rp));
+  BBTC_TRY(scratch.get(&pos_of_edge, m > 0 ? m : 1));
+  BBTC_TRY(dalloc_n(&pl.rp, pl.total_rp, s));
+  BBTC_TRY(dalloc_n(&pl.ci, m > 0 ? m : 1, s));
   BBTC_CUDA(cudaMemcpyAsync(d_rpb, pl.h_rpb, sizeof(int64_t) * (size_t)p * p,
                             cudaMemcpyHostToDevice, s));
-  k_edge_to_csr<<<grid_for(g->m, 256, 32), 256, 0, s>>>(g->esrc, g->colidx, g->rowptr, g->m,
-                                                        pl.cuts, p, d_rpb, pl.rp, by_block,
-                                                        by_csr);
+  BBTC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint64_t) * (size_t)pl.total_rp, s));
+  if (m > 0) {
+    k_bcsr_count<<<grid_for(m, 256, 32), 256, 0, s>>>(
+        g->esrc, g->colidx, m, pl.cuts, p, d_rpb, reinterpret_cast<unsigned long long *>(cnt),
+        start);
+    BBTC_LAUNCH_CHECK();
+  }
+  BBTC_TRY(exclusive_scan_u64(cnt, cnt, pl.total_rp, s));
+  if (m > 0) {
+    k_bcsr_fill<<<grid_for(m, 256, 32), 256, 0, s>>>(g->esrc, g->colidx, m, pl.cuts, p, d_rpb,
+                                                     cnt, start, pl.ci, pos_of_edge);
+    BBTC_LAUNCH_CHECK();
+    k_remap_positions<<<grid_for(m, 256, 32), 256, 0, s>>>(pl.ie_e, m, pos_of_edge);
+    BBTC_LAUNCH_CHECK();
+  }
+  k_bcsr_rowptr<<<grid_for(pl.total_rp, 256, 32), 256, 0, s>>>(cnt, pl.total_rp, pl.rp);
   BBTC_LAUNCH_CHECK();
+  dfree(pl.spl, s);
+  pl.spl = nullptr;
   return BBTC_OK;
 }
 

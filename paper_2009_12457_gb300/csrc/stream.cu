@@ -94,9 +94,11 @@ bbtc_status to_pinned(T **host, T **dev, int64_t count, cudaStream_t s) {
   return BBTC_OK;
 }
 
-// Moves the block arrays of a resident plan to pinned host memory.
-bbtc_status plan_to_host(Plan &pl, int64_t m, cudaStream_t s) {
+// Moves the block arrays of a resident plan to pinned host memory, as
+// physical per-block copies.
+bbtc_status plan_to_host(const bbtc_graph *g, Plan &pl, int64_t m, cudaStream_t s) {
   if (pl.streamed) return BBTC_OK;
+  BBTC_TRY(plan_physical_blocks(g, pl, s));
   BBTC_TRY(to_pinned(&pl.h_rp, &pl.rp, pl.total_rp, s));
   BBTC_TRY(to_pinned(&pl.h_ci, &pl.ci, m, s));
   BBTC_TRY(to_pinned(&pl.h_ie_u, &pl.ie_u, m, s));
@@ -150,7 +152,7 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
                                unsigned long long *task_cycles) {
   const int p = pl.p;
   const int64_t nt = pl.ntasks;
-  BBTC_TRY(plan_to_host(pl, g->m, s));
+  BBTC_TRY(plan_to_host(g, pl, g->m, s));
 
   // small plan tables on the host
   std::vector<WorkItem> items((size_t)pl.nitems);
@@ -367,6 +369,8 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
         d.ie_e = reinterpret_cast<const uint32_t *>(pool + o_ie + 2 * seg);
         d.ie_off = ie0(i, j);
         d.rp_ik = reinterpret_cast<const uint32_t *>(pool + o_ik);
+        d.rs_ik = 1;
+        d.rs_jk = 1;
         d.ci_ik = reinterpret_cast<const int32_t *>(pool + o_ik + align_up(4 * (size_t)(vsize(i) + 1)));
         d.ci_ik_off = col0(i, k);
         d.rp_jk = reinterpret_cast<const uint32_t *>(pool + o_jk);
