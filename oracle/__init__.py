@@ -3,7 +3,8 @@
 A plain, slow, single-threaded restatement (bbtc_oracle.c) of what the CUDA
 library computes, following the paper's steps in order: canonical simple edge
 set (Sec. 2), degree and non-decreasing degree order (Sec. 4.1), orientation
-u < v (Sec. 2), contiguous partition into p parts (Sec. 2, Sec. 4.1), task
+u < v (Sec. 2), contiguous partition into p parts (Sec. 2, Sec. 4.1; balanced on
+edges, or probe-based to bound the largest block, Sec. 4.4), task
 composition (Alg. 4), task estimate and order (Sec. 5), per-task counting with
 bbTC-Intersect (Alg. 5) or bbTC-HMap (Alg. 6), and the whole-graph counts of
 Alg. 2 / Alg. 3.
@@ -89,6 +90,16 @@ def _declare(lib):
     lib.orc_edge_support.argtypes = [i64, P, P, P]
     lib.orc_cuts.argtypes = [i64, P, i32, P]
     lib.orc_block_nnz.argtypes = [i64, P, P, i32, P, P]
+    lib.orc_pbd_grains.argtypes = [i32]
+    lib.orc_pbd_grains.restype = i32
+    lib.orc_pbd_grain_bounds.argtypes = [i64, P, P, i32, P]
+    lib.orc_pbd_prefix.argtypes = [i64, P, P, i32, P, P]
+    lib.orc_pbd_load.argtypes = [i32, P, i32, i32, i32, i32]
+    lib.orc_pbd_load.restype = i64
+    lib.orc_pbd_probe.argtypes = [i32, P, i32, i64, P]
+    lib.orc_pbd_probe.restype = i32
+    lib.orc_pbd_cuts.argtypes = [i64, P, P, i32, P]
+    lib.orc_pbd_cuts.restype = i64
     lib.orc_num_tasks.argtypes = [i32]
     lib.orc_num_tasks.restype = i64
     lib.orc_task_list.argtypes = [i32, P, P, P]
@@ -192,6 +203,49 @@ def cuts(n: int, rp, p: int) -> np.ndarray:
     return c
 
 
+def pbd_grains(p: int) -> int:
+    """Number of grains G of the probe-based partition for p parts."""
+    return int(_load().orc_pbd_grains(p))
+
+
+def pbd_grain_bounds(n: int, rp, ci, G: int) -> np.ndarray:
+    """Grain boundaries b[0..G], balanced on undirected degree."""
+    rp, ci = _c(rp, np.int64), _c(ci, np.int32)
+    b = np.empty(G + 1, dtype=np.int32)
+    _load().orc_pbd_grain_bounds(n, _p(rp), _p(ci), G, _p(b))
+    return b
+
+
+def pbd_prefix(n: int, rp, ci, G: int, b) -> np.ndarray:
+    """(G+1) x (G+1) int64 table: S[r][c] = edges from grains [0,r) into grains [0,c)."""
+    rp, ci, b = _c(rp, np.int64), _c(ci, np.int32), _c(b, np.int32)
+    S = np.empty((G + 1) * (G + 1), dtype=np.int64)
+    _load().orc_pbd_prefix(n, _p(rp), _p(ci), G, _p(b), _p(S))
+    return S.reshape(G + 1, G + 1)
+
+
+def pbd_load(S, r0: int, r1: int, c0: int, c1: int) -> int:
+    """Edges from grains [r0, r1) into grains [c0, c1), through the oracle's table."""
+    S = _c(S, np.int64)
+    return int(_load().orc_pbd_load(S.shape[0] - 1, _p(S), r0, r1, c0, c1))
+
+
+def pbd_probe(S, p: int, B: int):
+    """Probe(B): (passed, grain cuts x[0..p])."""
+    S = _c(S, np.int64)
+    x = np.zeros(p + 1, dtype=np.int32)
+    ok = _load().orc_pbd_probe(S.shape[0] - 1, _p(S), p, B, _p(x))
+    return bool(ok), x
+
+
+def pbd_cuts(n: int, rp, ci, p: int):
+    """(cuts c[0..p], B*) of the probe-based symmetric partition."""
+    rp, ci = _c(rp, np.int64), _c(ci, np.int32)
+    c = np.empty(p + 1, dtype=np.int32)
+    bstar = _load().orc_pbd_cuts(n, _p(rp), _p(ci), p, _p(c))
+    return c, int(bstar)
+
+
 def block_nnz(n: int, rp, ci, p: int, c) -> np.ndarray:
     """|G_ij| as a p x p int64 array (row-major)."""
     rp, ci, c = _c(rp, np.int64), _c(ci, np.int32), _c(c, np.int32)
@@ -271,16 +325,19 @@ def prepare(n: int, rowptr, colidx) -> dict:
 
 
 def bbtc(n: int, rowptr, colidx, p: int = 1, method: str = "intersect",
-         prep: dict | None = None, want_per_vertex: bool = False) -> dict:
+         prep: dict | None = None, want_per_vertex: bool = False,
+         partition: str = "edges") -> dict:
     """The whole bbTC pipeline in the paper's order, sequentially.
 
+    partition: "edges" (contiguous parts balanced on oriented edges) or "pbd"
+    (the probe-based partition that bounds the largest block).
     Returns the oriented CSR, cuts, block sizes, task list, estimates and order,
     per-task counts (Alg. 5 or Alg. 6, one task at a time in the estimate's
     order), the total, and optionally per-vertex counts.
     """
     pr = prep if prep is not None else prepare(n, rowptr, colidx)
     rp, ci = pr["rowptr"], pr["colidx"]
-    c = cuts(n, rp, p)
+    c = cuts(n, rp, p) if partition == "edges" else pbd_cuts(n, rp, ci, p)[0]
     nnz = block_nnz(n, rp, ci, p, c)
     tasks = task_list(p)
     est = exec_time(p, c, nnz)

@@ -107,6 +107,80 @@ def with_noise(n, rowptr, colidx, rng, dup=0.3, loops=3):
     return n, rp, ci
 
 
+def pbd_pins(check, rng):
+    """Pins of the probe-based partition, from the dense adjacency and by hand."""
+    # two disjoint K_64 (ids 0-63 and 64-127), p = 2: every vertex has degree 63,
+    # so grain t is vertex t and the order is the id order. Part 0 can hold clique
+    # 0 plus vertex 64 (which adds no edge to it) within B = C(64,2) = 2016, and
+    # part 1 then holds C(63,2) = 1953 edges with 63 edges in block (0,1). Any
+    # B < 2016 leaves a whole clique's 2016 edges in one block.
+    n2, rp2, ci2 = G.csr_from_edges(128, [(a + o, b + o) for o in (0, 64)
+                                          for a in range(64) for b in range(a + 1, 64)])
+    pr = oracle.prepare(n2, rp2, ci2)
+    c, bstar = oracle.pbd_cuts(n2, pr["rowptr"], pr["colidx"], 2)
+    check(bstar == 2016 and c.tolist() == [0, 65, 128], f"PBD two K_64: {bstar} {c.tolist()}")
+    # p = 1: one part, B* = m
+    c, bstar = oracle.pbd_cuts(n2, pr["rowptr"], pr["colidx"], 1)
+    check(bstar == pr["m"] and c.tolist() == [0, 128], "PBD p=1")
+
+    for trial in range(6):
+        n = int(rng.integers(40, 260))
+        g = G.gnp(n, float(rng.uniform(0.02, 0.3)), rng)
+        # skew the degrees: a few hubs joined to many vertices
+        A0 = G.dense_adjacency(*g)
+        for h in rng.choice(n, size=3, replace=False):
+            others = rng.random(n) < 0.6
+            A0[h, others] = 1
+            A0[others, h] = 1
+        np.fill_diagonal(A0, 0)
+        g = G.csr_from_edges(n, list(zip(*np.nonzero(np.triu(A0, 1)))))
+        A, deg, rank, perm, outdeg = positions_by_definition(*g)
+        pr = oracle.prepare(*g)
+        m = pr["m"]
+        Ar = np.zeros_like(A)                    # adjacency in position space, u < v
+        ar, br = np.nonzero(np.triu(A, 1))
+        lo_, hi_ = np.minimum(rank[ar], rank[br]), np.maximum(rank[ar], rank[br])
+        Ar[lo_, hi_] = 1
+        cum = np.zeros((n + 1, n + 1), dtype=np.int64)
+        cum[1:, 1:] = Ar.cumsum(0).cumsum(1)
+
+        def edges_in(u0, u1, v0, v1):
+            return int(cum[u1, v1] - cum[u0, v1] - cum[u1, v0] + cum[u0, v0])
+
+        for p in (2, 3, 5):
+            Gn = oracle.pbd_grains(p)
+            check(Gn == min(2048, 64 * p), f"grain count p={p}")
+            b = oracle.pbd_grain_bounds(n, pr["rowptr"], pr["colidx"], Gn)
+            # grains: b_t = min{ r : D(r) >= ceil(t*2m/G) }, D over undirected degree
+            D = np.concatenate([[0], np.cumsum(deg[perm])])
+            want = [0] + [int(np.searchsorted(D, -(-t * 2 * m // Gn), side="left"))
+                          for t in range(1, Gn)] + [n]
+            check(b.tolist() == want, f"PBD grain bounds p={p} trial {trial}")
+            S = oracle.pbd_prefix(n, pr["rowptr"], pr["colidx"], Gn, b)
+            for _ in range(30):
+                r0, r1 = sorted(int(x) for x in rng.integers(0, Gn + 1, 2))
+                c0, c1 = sorted(int(x) for x in rng.integers(0, Gn + 1, 2))
+                check(oracle.pbd_load(S, r0, r1, c0, c1) == edges_in(b[r0], b[r1], b[c0], b[c1]),
+                      f"PBD load ({r0},{r1},{c0},{c1}) trial {trial}")
+            c, bstar = oracle.pbd_cuts(n, pr["rowptr"], pr["colidx"], p)
+            nnz = oracle.block_nnz(n, pr["rowptr"], pr["colidx"], p, c)
+            check(int(nnz.max()) <= bstar, f"PBD blocks above B* p={p} trial {trial}")
+            check(c[0] == 0 and c[p] == n and np.all(np.diff(c) >= 0), f"PBD cuts valid p={p}")
+            ok, x = oracle.pbd_probe(S, p, bstar)
+            check(ok and np.array_equal(b[x], c), f"PBD probe(B*) p={p} trial {trial}")
+            nb = p * (p + 1) // 2
+            okm, _ = oracle.pbd_probe(S, p, bstar - 1)
+            check(bstar == -(-m // nb) or not okm, f"PBD bisection not converged p={p}")
+            # each closed part is maximal: one more grain breaks a block of its column
+            for i in range(p):
+                if x[i] == Gn or x[i + 1] == Gn:
+                    continue
+                t = int(x[i + 1]) + 1
+                loads = [edges_in(b[x[i]], b[t], b[x[i]], b[t])]
+                loads += [edges_in(b[x[k]], b[x[k + 1]], b[x[i]], b[t]) for k in range(i)]
+                check(max(loads) > bstar, f"PBD part {i} not maximal p={p} trial {trial}")
+
+
 def pin_battery() -> list[str]:
     fails: list[str] = []
 
@@ -181,6 +255,9 @@ def pin_battery() -> list[str]:
             check(np.array_equal(cls, brute), f"classified per task p={p} trial {trial}")
         if len(fails) > 20:
             break
+
+    # probe-based partition
+    pbd_pins(check, rng)
 
     # ExecTime on a hand-worked example: p=2, cuts [0,2,5],
     # |G_00|=3, |G_01|=4, |G_11|=6 -> delta(G_00)=1.5, delta(G_01)=2, delta(G_11)=2

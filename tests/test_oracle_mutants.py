@@ -44,6 +44,14 @@ MUTANTS = {
                              "g_sort_est[a] < g_sort_est[b] ? -1 : 1"),
     "task_count_formula": ("return (int64_t)p * (p + 1) * (p + 2) / 6;",
                            "return (int64_t)p * (p + 1) * (p + 1) / 6;"),
+    "pbd_weight_out_degree_only": ("    for (int64_t e = rp[u]; e < rp[u + 1]; ++e) w[ci[e]] += 1;\n", ""),
+    "pbd_load_sign": ("return S[r1 * W + c1] - S[r0 * W + c1] - S[r1 * W + c0] + S[r0 * W + c0];",
+                      "return S[r1 * W + c1] - S[r0 * W + c1] - S[r1 * W + c0] - S[r0 * W + c0];"),
+    "pbd_ignores_column_blocks": ("for (int32_t k = 0; ok && k < i; ++k)",
+                                  "for (int32_t k = 0; ok && k < 0; ++k)"),
+    "pbd_probe_not_greedy": ("      best = t;\n    }", "      best = t;\n      break;\n    }"),
+    "pbd_bisection_keeps_lo": ("if (orc_pbd_probe(G, S, p, mid, x)) hi = mid; else lo = mid;",
+                               "if (orc_pbd_probe(G, S, p, mid, x)) lo = mid; else hi = mid;"),
     "classify_drops_w_part": ("per_task[idx[((int64_t)bu * p + bv) * p + part_of(ci[a], p, cuts)]] += 1;",
                               "per_task[idx[((int64_t)bu * p + bv) * p + bv]] += 1;"),
 }

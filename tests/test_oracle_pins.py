@@ -225,3 +225,34 @@ def test_edge_support_brute_force():
             assert A[a, b] == 1 and s == common[a, b]
         T = oracle.tc_intersect(n, pr["rowptr"], pr["colidx"])
         assert sum(sup.values()) == 3 * T
+
+
+@pytest.mark.parametrize("p", [2, 3, 6])
+def test_pbd_pipeline_per_task(p):
+    """Under the probe-based cuts, Alg. 5 and Alg. 6 per task equal the
+    classification of every triangle into its task, and the total is unchanged."""
+    rng = np.random.default_rng(40 + p)
+    for _ in range(4):
+        n = int(rng.integers(30, 120))
+        g = G.gnp(n, float(rng.uniform(0.05, 0.4)), rng)
+        T = G.brute_force_triangles(*g)
+        r5 = oracle.bbtc(*g, p=p, method="intersect", partition="pbd")
+        r6 = oracle.bbtc(*g, p=p, method="hmap", partition="pbd", prep=r5)
+        c, _ = oracle.pbd_cuts(n, r5["rowptr"], r5["colidx"], p)
+        assert np.array_equal(r5["cuts"], c)
+        cls = oracle.classify_triangles(n, r5["rowptr"], r5["colidx"], p, c)
+        assert r5["total"] == T and r6["total"] == T
+        assert np.array_equal(r5["per_task"], cls) and np.array_equal(r6["per_task"], cls)
+
+
+def test_pbd_lowers_imbalance_on_rmat():
+    """Sec. 4.4: lambda = m_max / m_avg. On the skewed R-MAT scale-14 graph the
+    probe-based partition must not be worse than the edge-balanced one."""
+    n, rp, ci = graphgen.rmat(14, 16, 1)
+    pr = oracle.prepare(n, rp, ci)
+    for p in (2, 4, 8):
+        ce = oracle.cuts(n, pr["rowptr"], p)
+        cp, bstar = oracle.pbd_cuts(n, pr["rowptr"], pr["colidx"], p)
+        me = oracle.block_nnz(n, pr["rowptr"], pr["colidx"], p, ce).max()
+        mp = oracle.block_nnz(n, pr["rowptr"], pr["colidx"], p, cp).max()
+        assert mp <= bstar and mp <= me
