@@ -447,6 +447,9 @@ def main():
                     help="rmat-s23 (default), rmat-s14, chunglu-friendster, or rmat-sNN")
     ap.add_argument("--p", default="0", help="blocks per side; a comma list runs each")
     ap.add_argument("--kernel", default="auto", choices=["auto", "intersect", "hashmap"])
+    ap.add_argument("--partition", default="edges", choices=["edges", "probe"],
+                    help="edges: contiguous parts balanced on oriented edges; probe: "
+                         "probe-based partition bounding the largest block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--budget-gb", default="0",
                     help="comma list of device budgets (GB) for the counting step's blocks, "
@@ -509,7 +512,8 @@ def main():
                 h = bb.bbtc_graph_create_async(n, h_rp, h_ci, flags, stream)
             try:
                 total = bb.bbtc_count(h, bb.make_opts(p=p, kernel=args.kernel, stream=stream,
-                                                      device_budget_bytes=budget))
+                                                      device_budget_bytes=budget,
+                                                      partition=args.partition))
                 info = bb.bbtc_graph_get_info(h) if device_resident else None
                 tim = bb.bbtc_graph_get_timings(h) if device_resident else None
             finally:
@@ -564,6 +568,17 @@ def main():
         if len(totals) != 1:
             raise SystemExit(f"inconsistent triangle counts across steps: {sorted(totals)}")
 
+        # load imbalance of the partition (Sec. 4.4): lambda = m_max / m_avg over the
+        # p(p+1)/2 blocks, from one more (untimed) plan
+        h = bb.bbtc_graph_create_async(n, d_rp, d_ci, flags, stream)
+        try:
+            bb.bbtc_graph_plan(h, bb.make_opts(p=p, kernel=args.kernel, stream=stream,
+                                               partition=args.partition))
+            nnz = bb.bbtc_graph_get_plan(h, p)["block_nnz"]
+        finally:
+            bb.bbtc_graph_destroy(h)
+        lam = float(nnz.max()) / (m / (p * (p + 1) / 2)) if m else 1.0
+
         # pinned host-to-device bandwidth right now (streamed counts depend on it,
         # and it varies from box to box)
         h2d_gbs = None
@@ -607,7 +622,8 @@ def main():
                 "data": "synthetic",
                 "config": {
                     "workload": WORKLOADS.get(args.workload, args.workload), "p": p,
-                    "kernel": args.kernel,
+                    "kernel": args.kernel, "partition": args.partition,
+                    "lambda": lam, "max_block_nnz": int(nnz.max()),
                     "n": n, "m": m, "triangles": next(iter(totals)),
                     "input_entries": int(h_ci.numel()),
                     "l2": "inputs larger than L2 (input CSR %.2f GB, oriented CSR %.2f GB)"

@@ -57,6 +57,17 @@ typedef enum {
                                 value range when it fits on chip, else hash table */
 } bbtc_kernel;
 
+/* Symmetric partition of the degree order into p parts (Sec. 2 V^p, Sec. 4.1). */
+typedef enum {
+  BBTC_PARTITION_EDGES = 0, /* contiguous parts balanced on oriented edges:
+                               c_i = min{ r : rowptr[r] >= ceil(i*m/p) } */
+  BBTC_PARTITION_PROBE = 1  /* probe-based: bounds the largest block |G_ij| (Sec. 4.4's
+                               m_max, hence lambda) by bisection on a bound B, each
+                               probe closing part after part as late as its column's
+                               blocks stay within B; parts end on one of
+                               min(2048, 64p) grains balanced on undirected degree */
+} bbtc_partition;
+
 /* bbtc_graph_create flags */
 #define BBTC_INPUT_DEVICE 0x1u    /* rowptr/colidx are DEVICE pointers on the current device */
 #define BBTC_INPUT_SYMMETRIC 0x2u /* caller guarantees every edge is listed under both
@@ -84,7 +95,7 @@ typedef struct {
   uint64_t *per_graph_out;      /* NULL, or one uint64 per graph of a batch handle
                                    (bbtc_graph_create_batch / bbtc_count_batch) */
   int32_t chunk;                /* in-edges per work item of the counting kernel; 0 = auto */
-  int32_t reserved;             /* must be 0 */
+  int32_t partition;            /* bbtc_partition; part of the plan's identity like p */
   uint64_t *per_task_cycles_out; /* NULL, or bbtc_num_tasks(p) uint64 in Alg. 4 order: SM
                                     clock cycles the counting kernel's warps spent on each
                                     task's work items (the measured side of the Sec. 5
@@ -154,15 +165,17 @@ bbtc_status bbtc_graph_create_batch(int32_t ng, const int64_t *vertex_offsets,
 
 /*
  * Count the triangles of the handle's graph with bbTC at p x p blocks:
- * contiguous symmetric partition of the degree order balanced on oriented
- * edges, tasks (i,j,k), i <= j <= k (Alg. 4), ordered by the Sec. 5 estimate
+ * contiguous symmetric partition of the degree order (opts->partition:
+ * balanced on oriented edges, or probe-based to bound the largest block),
+ * tasks (i,j,k), i <= j <= k (Alg. 4), ordered by the Sec. 5 estimate
  * and drained by a persistent work-stealing kernel, each task counted as
  * sum over (u,v) in G_ij of |N(G_ik,u) ∩ N(G_jk,v)| (Alg. 5 / Alg. 6).
  *
  *   count  receives the exact total (host uint64)
  *   opts   NULL = defaults; see bbtc_opts for the optional outputs
  *
- * Errors: EINVAL (p outside 0..64, opts->struct_size too small), ENOMEM
+ * Errors: EINVAL (p outside 0..64, an unknown kernel or partition,
+ * opts->struct_size too small), ENOMEM
  * (also when device_budget_bytes cannot hold one task's blocks), ETIMEOUT,
  * ECUDA.
  */
@@ -170,7 +183,7 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts, uint64_t *count);
 
 /*
  * Build the resident plan of the handle for opts' p (0 = automatic), kernel,
- * hash_threshold and chunk -- partition, blocks, tasks, estimates and work
+ * hash_threshold, chunk and partition -- partition, blocks, tasks, estimates and work
  * items (Sec. 2, Sec. 4.1-4.2, Sec. 5) -- without counting; keep it when it
  * already matches. Later counts with the same options only read the plan.
  * Other options are ignored. Synchronous.
@@ -183,7 +196,7 @@ bbtc_status bbtc_graph_plan(bbtc_graph_t g, const bbtc_opts *opts);
  * all of them drained together).
  *
  * Resident (device_budget_bytes = 0): each handle keeps its own plan for
- * (p, kernel, hash_threshold, chunk) -- built first, on the handle, when it
+ * (p, kernel, hash_threshold, chunk, partition) -- built first, on the handle, when it
  * does not match -- and one counting launch takes the work items of all the
  * handles, largest handles first. p = 0 picks p per handle from its size.
  * Handles that already hold a matching resident plan are only read, so
@@ -196,8 +209,8 @@ bbtc_status bbtc_graph_plan(bbtc_graph_t g, const bbtc_opts *opts);
  *   counts     receives ng uint64 totals (host)
  *   per_graph  NULL, or receives each handle's status
  *
- * Options other than p, kernel, hash_threshold, chunk, timeout_ms, stream and
- * device_budget_bytes are ignored (no per-task, per-vertex or per-graph
+ * Options other than p, kernel, hash_threshold, chunk, partition, timeout_ms,
+ * stream and device_budget_bytes are ignored (no per-task, per-vertex or per-graph
  * outputs).
  * Errors: EINVAL for ng < 0, a NULL handle (its status is EINVAL and the
  * others are still counted) or handles on different devices; ENOMEM;
@@ -242,7 +255,7 @@ bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *count_dev,
 /*
  * Enqueue a count on opts->stream (NULL = the handle's stream) without
  * allocating and without waiting: the plan for (p, kernel, hash_threshold,
- * chunk) must already exist on the handle (built by bbtc_count or
+ * chunk, partition) must already exist on the handle (built by bbtc_count or
  * bbtc_graph_get_plan), and every output is a DEVICE pointer: total_dev (one
  * uint64), opts->per_task_out and opts->per_graph_out (nullable;
  * opts->flags must include BBTC_OUT_DEVICE when they are set);
@@ -309,7 +322,8 @@ bbtc_status bbtc_graph_get_oriented(bbtc_graph_t g, int64_t *rowptr, int32_t *co
 
 /*
  * The plan bbtc_count builds for p (Sec. 2, Sec. 4.2, Sec. 5), as host copies
- * (any output may be NULL): cuts p+1 int32 (c_0 = 0, c_p = n), block_nnz p*p
+ * (any output may be NULL); the handle's current plan when it has this p
+ * (whatever its partition), else a new one with the edge-balanced partition: cuts p+1 int32 (c_0 = 0, c_p = n), block_nnz p*p
  * int64 (|G_ij|, row-major), tasks 3*|T| int32 ((i,j,k) in Alg. 4 order),
  * estimate |T| double (ExecTime in Alg. 4 order), order |T| int32 (task
  * indices, non-increasing estimate, ties in Alg. 4 order).

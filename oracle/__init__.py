@@ -329,7 +329,7 @@ def bbtc(n: int, rowptr, colidx, p: int = 1, method: str = "intersect",
          partition: str = "edges") -> dict:
     """The whole bbTC pipeline in the paper's order, sequentially.
 
-    partition: "edges" (contiguous parts balanced on oriented edges) or "pbd"
+    partition: "edges" (contiguous parts balanced on oriented edges) or "probe"
     (the probe-based partition that bounds the largest block).
     Returns the oriented CSR, cuts, block sizes, task list, estimates and order,
     per-task counts (Alg. 5 or Alg. 6, one task at a time in the estimate's
@@ -337,7 +337,7 @@ def bbtc(n: int, rowptr, colidx, p: int = 1, method: str = "intersect",
     """
     pr = prep if prep is not None else prepare(n, rowptr, colidx)
     rp, ci = pr["rowptr"], pr["colidx"]
-    c = cuts(n, rp, p) if partition == "edges" else pbd_cuts(n, rp, ci, p)[0]
+    c = cuts(n, rp, p) if partition == "edges" else pbd_cuts(n, rp, ci, p)[0]  # "probe"
     nnz = block_nnz(n, rp, ci, p, c)
     tasks = task_list(p)
     est = exec_time(p, c, nnz)

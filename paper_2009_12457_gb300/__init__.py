@@ -30,6 +30,7 @@ __all__ = [
 STATUS = {0: "BBTC_OK", 1: "BBTC_EINVAL", 2: "BBTC_ENOMEM", 3: "BBTC_ECUDA",
           4: "BBTC_ETIMEOUT", 5: "BBTC_ECANCELLED", 6: "BBTC_EINTERNAL"}
 KERNELS = {"auto": 0, "intersect": 1, "hashmap": 2}
+PARTITIONS = {"edges": 0, "probe": 1}
 
 INPUT_DEVICE = 0x1
 INPUT_SYMMETRIC = 0x2
@@ -56,7 +57,7 @@ class bbtc_opts(ctypes.Structure):
         ("hash_threshold", ctypes.c_int32),
         ("per_graph_out", ctypes.c_void_p),
         ("chunk", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("partition", ctypes.c_int32),
         ("per_task_cycles_out", ctypes.c_void_p),
         ("per_edge_out", ctypes.c_void_p),
     ]
@@ -215,8 +216,10 @@ def bbtc_graph_destroy(handle: int) -> None:
 def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
               device_budget_bytes: int = 0, per_vertex_out=None, per_task_out=None,
               stream=None, hash_threshold: int = 0, per_graph_out=None,
-              chunk: int = 0, per_task_cycles_out=None, per_edge_out=None) -> bbtc_opts:
+              chunk: int = 0, per_task_cycles_out=None, per_edge_out=None,
+              partition: str | int = "edges") -> bbtc_opts:
     o = bbtc_opts_init()
+    o.partition = PARTITIONS[partition] if isinstance(partition, str) else int(partition)
     o.p = p
     o.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     o.timeout_ms = timeout_ms
@@ -349,7 +352,8 @@ class Graph:
     def count(self, p: int = 0, kernel: str = "auto", per_vertex: bool = False,
               per_task: bool = False, timeout_ms: int = 0, device_budget_bytes: int = 0,
               stream=None, hash_threshold: int = 0, per_graph: bool = False, chunk: int = 0,
-              per_task_cycles: bool = False, per_edge: bool = False):
+              per_task_cycles: bool = False, per_edge: bool = False,
+              partition: str = "edges"):
         """Total triangle count, or a dict with per-task / per-vertex / per-graph counts
         (with per_task_cycles, the SM cycles spent on each task; with per_edge, the
         support of each oriented edge in the order of get_oriented()'s colidx)."""
@@ -365,7 +369,7 @@ class Graph:
         m = self.info()["m"] if per_edge else 0
         pe = np.zeros(max(m, 1), dtype=np.uint32) if per_edge else None
         opts = make_opts(p, kernel, timeout_ms, device_budget_bytes, pv, pt, stream,
-                         hash_threshold, pg, chunk, cyc, pe)
+                         hash_threshold, pg, chunk, cyc, pe, partition)
         total = bbtc_count(self.handle, opts)
         if not (per_task or per_vertex or per_graph or per_task_cycles or per_edge):
             return total
@@ -396,7 +400,11 @@ class Graph:
     def oriented(self) -> dict:
         return bbtc_graph_get_oriented(self.handle)
 
-    def plan(self, p: int) -> dict:
+    def plan(self, p: int, partition: str | None = None) -> dict:
+        """The plan for p: the handle's current one for p, or first built with
+        `partition` when given."""
+        if partition is not None:
+            bbtc_graph_plan(self.handle, make_opts(p=p, partition=partition))
         return bbtc_graph_get_plan(self.handle, p)
 
     def timings(self) -> dict:

@@ -133,8 +133,12 @@ bbtc_status check_opts(const bbtc_opts *opts, bbtc_opts *out) {
     return BBTC_EINVAL;
   }
   if (out->hash_threshold == 0) out->hash_threshold = 16;
-  if (out->chunk < 0 || out->reserved != 0) {
-    set_error("chunk = %d must be >= 0 and reserved must be 0", out->chunk);
+  if (out->chunk < 0) {
+    set_error("chunk = %d must be >= 0", out->chunk);
+    return BBTC_EINVAL;
+  }
+  if (out->partition != BBTC_PARTITION_EDGES && out->partition != BBTC_PARTITION_PROBE) {
+    set_error("partition = %d is not a bbtc_partition", out->partition);
     return BBTC_EINVAL;
   }
   return BBTC_OK;
@@ -359,9 +363,10 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   // a resident count needs the block arrays on the device: a plan that was
   // streamed (its arrays now in host memory) is rebuilt
   if (!budgeted && g->plan.streamed) free_plan(&g->plan, s);
-  const bool rebuild = !plan_matches(g->plan, p, opts.kernel, opts.hash_threshold, opts.chunk);
+  const bool rebuild =
+      !plan_matches(g->plan, p, opts.kernel, opts.hash_threshold, opts.chunk, opts.partition);
   if (rebuild) BBTC_CUDA(cudaEventRecord(g->ev[2], s));
-  BBTC_TRY(build_plan(g, p, opts.kernel, opts.hash_threshold, opts.chunk, s));
+  BBTC_TRY(build_plan(g, p, opts.kernel, opts.hash_threshold, opts.chunk, s, opts.partition));
   if (rebuild) BBTC_CUDA(cudaEventRecord(g->ev[3], s));
   g->plan_timed = rebuild;
   const Plan &pl = g->plan;
@@ -436,7 +441,7 @@ bbtc_status bbtc_count_async(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t 
   bbtc_opts opts;
   BBTC_TRY(check_opts(opts_in, &opts));
   const int p = opts.p == 0 ? default_p(g) : opts.p;
-  if (!plan_matches(g->plan, p, opts.kernel, opts.hash_threshold, opts.chunk) ||
+  if (!plan_matches(g->plan, p, opts.kernel, opts.hash_threshold, opts.chunk, opts.partition) ||
       g->plan.streamed) {
     set_error("bbtc_count_async: no resident plan for these options on the handle; build it "
               "with bbtc_count (without a device budget) or bbtc_graph_get_plan first");
@@ -476,7 +481,7 @@ bbtc_status bbtc_graph_plan(bbtc_graph_t g, const bbtc_opts *opts_in) {
   const int p = opts.p == 0 ? default_p(g) : opts.p;
   cudaStream_t s = opts.stream ? (cudaStream_t)opts.stream : g->stream;
   if (g->plan.streamed) free_plan(&g->plan, s);
-  BBTC_TRY(build_plan(g, p, opts.kernel, opts.hash_threshold, opts.chunk, s));
+  BBTC_TRY(build_plan(g, p, opts.kernel, opts.hash_threshold, opts.chunk, s, opts.partition));
   BBTC_CUDA(cudaStreamSynchronize(s));
   return BBTC_OK;
 }
@@ -531,7 +536,7 @@ bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts
       bbtc_graph *h = valid[x];
       const int p = o.p == 0 ? default_p(h) : o.p;
       if (h->plan.streamed) free_plan(&h->plan, s);
-      st = build_plan(h, p, o.kernel, o.hash_threshold, o.chunk, s);
+      st = build_plan(h, p, o.kernel, o.hash_threshold, o.chunk, s, o.partition);
     }
     uint64_t *sub = st == BBTC_OK ? new (std::nothrow) uint64_t[(size_t)nv] : nullptr;
     if (st == BBTC_OK && !sub) st = BBTC_ENOMEM;
@@ -679,7 +684,8 @@ bbtc_status bbtc_graph_get_plan(bbtc_graph_t g, int32_t p, int32_t *cuts, int64_
   const int kmode = g->plan.p == p ? g->plan.kernel_mode : BBTC_KERNEL_AUTO;
   const int thr = g->plan.p == p ? g->plan.hash_threshold : 16;
   const int chunk = g->plan.p == p ? g->plan.chunk_req : 0;
-  BBTC_TRY(build_plan(g, p, kmode, thr, chunk, s));
+  const int part = g->plan.p == p ? g->plan.partition : BBTC_PARTITION_EDGES;
+  BBTC_TRY(build_plan(g, p, kmode, thr, chunk, s, part));
   const Plan &pl = g->plan;
   if (cuts)
     BBTC_CUDA(cudaMemcpyAsync(cuts, pl.cuts, sizeof(int32_t) * (size_t)(p + 1),

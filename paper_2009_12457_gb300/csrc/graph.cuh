@@ -77,6 +77,8 @@ struct Plan {
   int32_t kernel_mode = -1;     // bbtc_kernel the items were built for
   int32_t hash_threshold = 0;
   int32_t chunk_req = 0;        // requested in-edges per item (0 = automatic)
+  int32_t partition = 0;        // bbtc_partition the cuts were built with
+  int64_t bstar = -1;           // probe-based partition: the bound B* on every block
   int64_t chunk = 0;            // in-edges per item used
   // counting scratch owned by the plan: [0] work-stealing head, [1] status,
   // [2] total, [3, 3+T) per-task counts, [3+T, 3+T+ng) per-graph counts
@@ -138,12 +140,20 @@ bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t 
                           int64_t nnz, bool symmetric);
 
 // a5-a8: partition, blocks, tasks, estimate, order and work items for p.
+// partition: 0 = contiguous parts balanced on oriented edges, 1 = probe-based
+// (bounds the largest block).
 bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold, int chunk,
-                       cudaStream_t s);
-inline bool plan_matches(const Plan &pl, int p, int kernel_mode, int hash_threshold, int chunk) {
+                       cudaStream_t s, int partition = 0);
+inline bool plan_matches(const Plan &pl, int p, int kernel_mode, int hash_threshold, int chunk,
+                         int partition = 0) {
   return pl.p == p && pl.kernel_mode == kernel_mode && pl.hash_threshold == hash_threshold &&
-         pl.chunk_req == chunk;
+         pl.chunk_req == chunk && pl.partition == partition;
 }
+
+// a5, probe-based: cuts (device, p+1) of the partition that bounds the largest
+// block load by B* (returned on the host). Synchronises s.
+bbtc_status pbd_partition(const bbtc_graph *g, int p, int32_t *d_cuts, int64_t *h_bstar,
+                          cudaStream_t s);
 void free_plan(Plan *pl, cudaStream_t s);
 void free_plan_host(Plan *pl);  // pinned host copies of a streamed plan
 

@@ -1,6 +1,7 @@
 // plan.cu -- per-p planning steps of bbTC (run by bbtc_count, cached per p):
 //   a5 partition: contiguous cuts of the degree order balanced on oriented
-//      edges (Sec. 2 vertex partition V^p; Sec. 4.1 symmetric partition)
+//      edges (Sec. 2 vertex partition V^p; Sec. 4.1 symmetric partition),
+//      or the probe-based partition of partition.cu
 //   a6 blocks G_ij = {(u,v) : u in V_i, v in V_j} (Sec. 2), materialised as
 //      the in-edges of each v grouped by the part of their source, so that a
 //      block's edges are one contiguous, destination-ordered range
@@ -386,14 +387,15 @@ int default_p(const bbtc_graph *g) {
 }
 
 bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold, int chunk_req,
-                       cudaStream_t s) {
-  if (plan_matches(g->plan, p, kernel_mode, hash_threshold, chunk_req)) return BBTC_OK;
+                       cudaStream_t s, int partition) {
+  if (plan_matches(g->plan, p, kernel_mode, hash_threshold, chunk_req, partition)) return BBTC_OK;
   free_plan(&g->plan, s);
   Plan pl;
   pl.p = p;
   pl.kernel_mode = kernel_mode;
   pl.hash_threshold = hash_threshold;
   pl.chunk_req = chunk_req;
+  pl.partition = partition;
   pl.ntasks = (int64_t)p * (p + 1) * (p + 2) / 6;
   const int64_t n = g->n, m = g->m;
   const int nb = g->nb;
@@ -410,8 +412,12 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
 
   // a5: cuts
   PLAN_TRY(dalloc_n(&pl.cuts, p + 1, s));
-  k_cuts<<<1, MAXP + 1, 0, s>>>(g->rowptr, n, p, pl.cuts);
-  PLAN_TRY(launch_status("build_plan"));
+  if (partition == 1) {
+    PLAN_TRY(pbd_partition(g, p, pl.cuts, &pl.bstar, s));
+  } else {
+    k_cuts<<<1, MAXP + 1, 0, s>>>(g->rowptr, n, p, pl.cuts);
+    PLAN_TRY(launch_status("build_plan"));
+  }
 
   // a6: the blocks, read in place from the oriented CSR through the split
   // table (per part a: |V_a| rows of p - a + 1 positions)

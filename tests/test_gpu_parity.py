@@ -255,3 +255,47 @@ def test_per_edge_support_large_sampled():
         na = set(ci[rp[a]:rp[a + 1]].tolist()) - {a}
         nb = set(ci[rp[b]:rp[b + 1]].tolist()) - {b}
         assert s[e] == len(na & nb), (a, b)
+
+
+def check_probe_partition(g, ps):
+    """Probe-based partition: cuts, block sizes, per-task and total counts equal the
+    oracle's (bbtc_graph_plan with the partition, then the plan read back)."""
+    n, rp, ci = g
+    ref = oracle.prepare(n, rp, ci)
+    with bb.Graph(n, rp, ci) as dev:
+        for p in ps:
+            r = oracle.bbtc(n, rp, ci, p=p, prep=ref, partition="probe")
+            plan = dev.plan(p, partition="probe")
+            assert np.array_equal(plan["cuts"], r["cuts"]), (p, plan["cuts"], r["cuts"])
+            assert np.array_equal(plan["block_nnz"], r["block_nnz"])
+            assert np.array_equal(plan["exec_time"], r["exec_time"])
+            assert np.array_equal(plan["order"], r["order"])
+            for kern in KERNELS:
+                out = dev.count(p=p, kernel=kern, per_task=True, partition="probe")
+                assert out["total"] == r["total"]
+                assert np.array_equal(out["per_task"], r["per_task"])
+            # and back to the edge-balanced partition on the same handle
+            assert np.array_equal(dev.plan(p, partition="edges")["cuts"],
+                                  oracle.cuts(n, ref["rowptr"], p))
+
+
+def test_probe_partition_config1():
+    check_probe_partition(graphgen.rmat_s14(), (1, 2, 3, 4, 8, 16))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_probe_partition_random(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(1, 500))
+    g = pins.with_noise(*G.gnp(n, float(rng.uniform(0.0, 0.4)), rng), rng, dup=0.2, loops=3)
+    check_probe_partition(g, (1, 2, 5, 7))
+
+
+def test_probe_partition_edge_cases():
+    check_probe_partition(G.csr_from_edges(10, []), (1, 3))        # no edges
+    check_probe_partition(G.complete(3), (1, 2, 4))                # more parts than vertices
+    two_k64 = G.csr_from_edges(128, [(a + o, b + o) for o in (0, 64)
+                                      for a in range(64) for b in range(a + 1, 64)])
+    check_probe_partition(two_k64, (2, 3))
+    # p = 64 (2048 grains) on an R-MAT graph of scale 12
+    check_probe_partition(graphgen.rmat(12, 16, 9), (64,))

@@ -236,8 +236,8 @@ def test_pbd_pipeline_per_task(p):
         n = int(rng.integers(30, 120))
         g = G.gnp(n, float(rng.uniform(0.05, 0.4)), rng)
         T = G.brute_force_triangles(*g)
-        r5 = oracle.bbtc(*g, p=p, method="intersect", partition="pbd")
-        r6 = oracle.bbtc(*g, p=p, method="hmap", partition="pbd", prep=r5)
+        r5 = oracle.bbtc(*g, p=p, method="intersect", partition="probe")
+        r6 = oracle.bbtc(*g, p=p, method="hmap", partition="probe", prep=r5)
         c, _ = oracle.pbd_cuts(n, r5["rowptr"], r5["colidx"], p)
         assert np.array_equal(r5["cuts"], c)
         cls = oracle.classify_triangles(n, r5["rowptr"], r5["colidx"], p, c)
