@@ -239,6 +239,11 @@ def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
     o.per_edge_out = outs[4][0][0] or None
     o.flags = OUT_DEVICE if kinds == {True} else 0
     o.stream = _stream_ptr(stream) or None
+    # the struct holds raw pointers: keep the output arrays (and the stream) alive
+    # for as long as the options are, so a temporary passed here is not freed
+    # before the library writes into it
+    o._keep = (per_vertex_out, per_task_out, per_graph_out, per_task_cycles_out,
+               per_edge_out, stream)
     return o
 
 

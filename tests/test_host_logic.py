@@ -82,3 +82,21 @@ def test_estimates_from_a_plan():
     assert np.allclose(e["degree"], [4.5, 1.5 + 2 + 2, 2 + 2 + 2, 6])
     assert np.allclose(e["density"], [3 * 0.75, 0.75 + 4 / 6 + 4 / 6, 4 / 6 + 6 / 9 + 4 / 6, 3 * 6 / 9])
     assert np.allclose(e["bbtc"], [4.5, 6.0, 8.0, 12.0])
+
+
+def test_opts_keep_output_arrays_alive():
+    """bbtc_opts holds raw pointers; make_opts must keep the arrays behind them
+    alive, so that a temporary output is not freed before the library writes it."""
+    import gc
+    import weakref
+    import numpy as np
+    import paper_2009_12457_gb300 as bb
+    arr = np.zeros(4096, dtype=np.uint64)
+    ref = weakref.ref(arr)
+    opts = bb.make_opts(p=2, per_graph_out=arr)
+    del arr
+    gc.collect()
+    assert ref() is not None and opts.per_graph_out == ref().ctypes.data
+    del opts
+    gc.collect()
+    assert ref() is None
