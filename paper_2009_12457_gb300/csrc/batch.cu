@@ -126,7 +126,7 @@ bbtc_status union_of(const bbtc_graph_t *gs, int32_t ng, cudaStream_t s, bbtc_gr
       }
   }
   if (st == BBTC_OK) st = dalloc_n(&u->rowptr, N + 1, s);
-  if (st == BBTC_OK) st = dalloc_n(&u->colidx, M, s);
+  if (st == BBTC_OK) st = dalloc_n(&u->colidx, padded_columns(M), s);
   if (st == BBTC_OK) st = dalloc_n(&u->esrc, M, s);
   if (st == BBTC_OK) st = dalloc_n(&u->perm, N, s);
   if (st == BBTC_OK) st = dalloc_n(&u->gid, N, s);

@@ -94,7 +94,8 @@ struct LaneRec {
   int64_t b0[32];     // N(G_jk, v) range of each lane (mixed batches only)
   int64_t b1[32];
   uint32_t s0[32];    // first probe element (local column index) of each lane's in-edge
-  uint32_t incl[32];  // inclusive prefix of the probe counts
+  uint32_t s1[32];    // one past its last probe element (quad probes only)
+  uint32_t incl[32];  // inclusive prefix of the probe counts (quad counts for quad probes)
   int32_t u[32];
   int32_t v[32];
 };
@@ -161,6 +162,63 @@ __device__ __forceinline__ void probe_batch(const int32_t *__restrict__ ci_ik, c
     for (int r = 0; r < U; ++r)
       if (own[r] >= 0 && lookup(wv[r], own[r])) on_hit(wv[r], own[r], qpos[r]);
   }
+}
+
+// Quad probes (plain counts against a bitmap-staged list): the probe range
+// [s0, s1) of each in-edge is widened down to a multiple of four, cut into
+// aligned groups of four columns ("quads"), and the quads of the batch are
+// flattened like single probes: lane l takes quads l, l + 32, ... and loads
+// each with one 16-byte load. A 4-bit mask per quad keeps the columns inside
+// [s0, s1). Column arrays are 16-byte aligned and padded by whole quads, so
+// the widened reads stay inside them. UQ quads per lane are in flight.
+__device__ __forceinline__ uint32_t quad_mask(uint32_t q, uint32_t lo, uint32_t hi) {
+  // columns q + c, 0 <= c < 4, with lo <= q + c < hi (q <= hi - 1, q >= lo - 3)
+  const uint32_t first = lo > q ? lo - q : 0u;
+  const uint32_t last = hi - q < 4u ? hi - q : 4u;
+  return ((1u << last) - 1u) & ~((1u << first) - 1u);
+}
+
+template <int UQ, typename Lookup>
+__device__ __forceinline__ uint32_t probe_quads(const int32_t *__restrict__ ci,
+                                                const LaneRec &rec, uint32_t totalq,
+                                                unsigned lane, Lookup lookup) {
+  uint32_t hits = 0;
+  int o = 0;
+  uint32_t o_end = rec.incl[0];
+  uint32_t lo = rec.s0[0], hi = rec.s1[0];
+  uint32_t base = lo & ~3u;  // column of quad j is base + 4 * j (mod 2^32)
+  uint32_t jb = lane;
+  for (; jb - lane < totalq; jb += 32u * UQ) {
+    int4 wq[UQ];
+    uint32_t msk[UQ];
+#pragma unroll
+    for (int r = 0; r < UQ; ++r) {
+      const uint32_t j = jb + 32u * r;
+      msk[r] = 0u;
+      wq[r] = make_int4(0, 0, 0, 0);
+      if (j < totalq) {
+        while (j >= o_end) {
+          ++o;
+          const uint32_t prev_end = o_end;
+          o_end = rec.incl[o];
+          lo = rec.s0[o];
+          hi = rec.s1[o];
+          base = (lo & ~3u) - 4u * prev_end;
+        }
+        const uint32_t q = base + 4u * j;
+        wq[r] = *reinterpret_cast<const int4 *>(ci + q);
+        msk[r] = quad_mask(q, lo, hi);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < UQ; ++r) {
+      hits += lookup(wq[r].x) & msk[r];
+      hits += lookup(wq[r].y) & (msk[r] >> 1);
+      hits += lookup(wq[r].z) & (msk[r] >> 2);
+      hits += lookup(wq[r].w) & (msk[r] >> 3);
+    }
+  }
+  return hits;
 }
 
 constexpr int UNIFORM_MIN = 4;  // a run of >= 4 in-edges into one v is a uniform batch
@@ -347,6 +405,28 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
             staged = true;
           }
         }
+      }
+
+      if (MODE == 0 && staged && staged_mode == ST_BITMAP) {
+        // quad probes (see probe_quads)
+        const uint32_t a0 = (uint32_t)s0 & ~3u;
+        const uint32_t nq = len ? ((uint32_t)s1 - a0 + 3u) >> 2 : 0u;
+        const uint32_t inclq = warp_inclusive_scan(nq);
+        const uint32_t totalq = __shfl_sync(0xffffffffu, inclq, 31);
+        rec.s0[lane] = (uint32_t)s0;
+        rec.s1[lane] = (uint32_t)s1;
+        rec.incl[lane] = inclq;
+        __syncwarp();
+        const unsigned *__restrict__ bm = reinterpret_cast<const unsigned *>(stage);
+        const int32_t first = staged_first;
+        const uint32_t span = (uint32_t)staged_len;
+        acc += probe_quads<1>(ci_ik, rec, totalq, lane, [&](int32_t w) -> uint32_t {
+          const uint32_t dlt = (uint32_t)(w - first);
+          const uint32_t word = bm[min(dlt >> 5, (uint32_t)(STAGE - 1))];
+          return (uint32_t)(dlt < span) & (word >> (dlt & 31u));
+        });
+        __syncwarp();
+        continue;
       }
 
       // flattened probes, interleaved over the lanes (lanes that share an

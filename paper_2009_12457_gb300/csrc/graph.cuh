@@ -5,6 +5,12 @@
 
 namespace bbtc {
 
+// Entries allocated for a column array of m entries: the counting kernel reads
+// columns as aligned groups of four, up to three entries past a list's end, so
+// every column array is padded to a multiple of four entries and one group
+// more (the extra entries are never counted).
+inline int64_t padded_columns(int64_t m) { return ((m + 3) & ~int64_t(3)) + 4; }
+
 // Where the counting kernel finds the three blocks of task t = (i, j, k):
 //  - the in-edges of G_ij (source u, destination v, position of (u,v) among
 //    the columns), grouped by v: element x of the task's range lives at

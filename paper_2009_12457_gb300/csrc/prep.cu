@@ -601,7 +601,7 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
     return BBTC_EINVAL;
   }
   g->m = m;
-  BBTC_TRY(dalloc_n(&g->colidx, m, s));
+  BBTC_TRY(dalloc_n(&g->colidx, padded_columns(m), s));
   BBTC_TRY(dalloc_n(&g->esrc, m, s));
   g->bytes += (uint64_t)(m > 0 ? m : 1) * 8;
   unsigned int *cursor = nullptr;
@@ -774,7 +774,7 @@ bbtc_status prepare_graph(bbtc_graph *g, const int64_t *d_rowptr, const int32_t 
 
   // ---- a4: orient and build the oriented CSR
   BBTC_TRY(dalloc_n(&g->rowptr, n + 1, s));
-  BBTC_TRY(dalloc_n(&g->colidx, m, s));
+  BBTC_TRY(dalloc_n(&g->colidx, padded_columns(m), s));
   BBTC_TRY(dalloc_n(&g->esrc, m, s));
   g->bytes += (uint64_t)(n + 1) * 8 + (uint64_t)(m > 0 ? m : 1) * 8;
   BBTC_CUDA(cudaMemsetAsync(g->rowptr, 0, sizeof(int64_t) * (size_t)(n + 1), s));
