@@ -231,8 +231,9 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
   extern __shared__ __align__(16) unsigned char count_smem_raw[];
   const unsigned lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
-  int32_t *stage = reinterpret_cast<int32_t *>(count_smem_raw) + warp * STAGE;
-  LaneRec &rec = reinterpret_cast<LaneRec *>(count_smem_raw + (size_t)(CT_NT / 32) * STAGE *
+  int32_t *stage = reinterpret_cast<int32_t *>(count_smem_raw) + warp * (STAGE + 4);
+  if (lane == 0) stage[STAGE] = 0;  // guard word after the stage: always zero
+  LaneRec &rec = reinterpret_cast<LaneRec *>(count_smem_raw + (size_t)(CT_NT / 32) * (STAGE + 4) *
                                                                   sizeof(int32_t))[warp];
   const uint64_t t_start = P.timeout_ns ? global_ns() : 0;
   // (task, v) whose N(G_jk, v) is in `stage`, and how it is stored
@@ -295,6 +296,14 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         nb = (base + 32 < w.x1 && last_head > 0) ? last_head : nvalid;
       }
       base += nb;
+      {  // the next batch's in-edge records, into L2 while this batch runs
+        const int64_t xn = base + lane;
+        if (xn < w.x1) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(ie_v + (xn - ie_off)));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(ie_u + (xn - ie_off)));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(ie_e + (xn - ie_off)));
+        }
+      }
       const bool active = (int)lane < nb;
 
       int32_t u = 0;
@@ -366,7 +375,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
           if (mode != ST_NONE) {
             __syncwarp();
             if (mode == ST_BITMAP) {
-              const int words4 = (int)(((span + 31) >> 5) + 3) >> 2;
+              const int words4 = STAGE / 4;  // the whole bitmap: bits past the span stay 0
               int4 *s4 = reinterpret_cast<int4 *>(stage);
               for (int i = lane; i < words4; i += 32) s4[i] = make_int4(0, 0, 0, 0);
               __syncwarp();
@@ -408,7 +417,8 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
       }
 
       if (MODE == 0 && staged && staged_mode == ST_BITMAP) {
-        // quad probes (see probe_quads)
+        // quad probes (see probe_quads); hash-table and sorted lookups keep the
+        // single-probe loop below, which measured faster for them
         const uint32_t a0 = (uint32_t)s0 & ~3u;
         const uint32_t nq = len ? ((uint32_t)s1 - a0 + 3u) >> 2 : 0u;
         const uint32_t inclq = warp_inclusive_scan(nq);
@@ -419,11 +429,11 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         __syncwarp();
         const unsigned *__restrict__ bm = reinterpret_cast<const unsigned *>(stage);
         const int32_t first = staged_first;
-        const uint32_t span = (uint32_t)staged_len;
-        acc += probe_quads<1>(ci_ik, rec, totalq, lane, [&](int32_t w) -> uint32_t {
+        acc += probe_quads<2>(ci_ik, rec, totalq, lane, [&](int32_t w) -> uint32_t {
           const uint32_t dlt = (uint32_t)(w - first);
-          const uint32_t word = bm[min(dlt >> 5, (uint32_t)(STAGE - 1))];
-          return (uint32_t)(dlt < span) & (word >> (dlt & 31u));
+          // values outside [first, first + STAGE * 32) read the zero guard word
+          const uint32_t word = bm[min(dlt >> 5, (uint32_t)STAGE)];
+          return (word >> (dlt & 31u)) & 1u;
         });
         __syncwarp();
         continue;
@@ -543,7 +553,7 @@ __global__ void k_wedges(const int64_t *__restrict__ rowptr, const int32_t *__re
 }
 
 size_t count_smem_bytes() {
-  return (size_t)(CT_NT / 32) * (STAGE * sizeof(int32_t) + sizeof(LaneRec));
+  return (size_t)(CT_NT / 32) * ((STAGE + 4) * sizeof(int32_t) + sizeof(LaneRec));
 }
 
 template <int MODE>

@@ -286,7 +286,8 @@ __global__ void k_tile_rows(const int64_t *__restrict__ rowptr, int64_t n, int64
 }
 
 // Pass over the entries: thread t of a tile owns entries [t*8, t*8+8) and walks
-// their rows forward from one search inside the tile's row window. MODE 0:
+// their rows forward from one search inside the tile's row window; the counts
+// of a row are added once per thread. MODE 0:
 // degree of u += first copies of v != u, flag unsorted rows and out-of-range
 // ids. MODE 1: out-degree at rank(u) += first copies with rank(v) > rank(u).
 // MODE 2: scatter rank(v) into row rank(u) (any order; rows are sorted after).
@@ -328,12 +329,17 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
       gbase = voff[gi];
       gend = voff[gi + 1];
     }
+    // key of each item: MODE 0 its row u when it is the first copy of a
+    // neighbour != u; MODE 1/2 rank(u) when it is such a copy and points up;
+    // else -1. Keys >= 0 never decrease along a thread's items (rows ascend), so
+    // equal keys form one group per row and each group costs one atomic.
+    int64_t key[SP_ITEMS];
+    int32_t val[SP_ITEMS];  // MODE 2: rank(v)
 #pragma unroll
     for (int i = 0; i < SP_ITEMS; ++i) {
       const int64_t e = first + i;
-      bool head = false;
-      int32_t v = 0;
-      bool first_in_row = false;
+      key[i] = -1;
+      val[i] = 0;
       if (e < t1) {
         while (e >= row_end) {  // next non-empty row
           ++u;
@@ -348,37 +354,68 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
           }
         }
         const int32_t vl = colidx[e];  // local to the row's graph
-        first_in_row = e == rowptr[u];
+        const bool first_in_row = e == rowptr[u];
         const int32_t prev = first_in_row ? -1 : colidx[e - 1];
         const bool in_range = vl >= 0 && (int64_t)vl < gend - gbase;
         if (MODE == 0) {
           if (!in_range) atomicOr(err, 2);
           else if (!first_in_row && prev > vl) atomicOr(err, 4);
         }
-        v = in_range ? (int32_t)(vl + gbase) : 0;
-        head = in_range && v != u && (first_in_row || prev != vl);
+        const int32_t v = in_range ? (int32_t)(vl + gbase) : 0;
+        const bool head = in_range && v != u && (first_in_row || prev != vl);
+        if (MODE == 0) {
+          key[i] = head ? u : -1;
+        } else if (head) {
+          const int32_t rv = rank[v];
+          if (rv > ru) key[i] = ru;
+          val[i] = rv;
+        }
       }
-      if (MODE == 0) {
-        const int64_t key = head ? u : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (key >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&deg[key], __popc(peers));
-      } else {
-        const bool up = head && rank[v] > ru;
-        const int64_t key = up ? (int64_t)ru : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const int leader = __ffs(peers) - 1;
-        if (MODE == 1) {
-          if (key >= 0 && (int)lane == leader)
-            atomicAdd(&dplus[key], (unsigned long long)__popc(peers));
-        } else {
-          unsigned base = 0;
-          if (key >= 0 && (int)lane == leader) base = atomicAdd(&cursor[key], (unsigned)__popc(peers));
-          base = __shfl_sync(0xffffffffu, base, leader);
-          if (key >= 0) {
-            const int64_t pos = rowptr_o[key] + base + __popc(peers & ((1u << lane) - 1u));
-            colidx_o[pos] = rank[v];
-            esrc_o[pos] = (int32_t)key;
+    }
+    if (MODE < 2) {
+      int64_t cur = -1;
+      unsigned cnt = 0;
+      int groups = 0;
+#pragma unroll
+      for (int i = 0; i < SP_ITEMS; ++i) {
+        if (key[i] >= 0 && key[i] != cur) {
+          if (cur >= 0) {
+            if (MODE == 0) atomicAdd(&deg[cur], (int)cnt);
+            else atomicAdd(&dplus[cur], (unsigned long long)cnt);
           }
+          cur = key[i];
+          cnt = 0;
+          ++groups;
+        }
+        if (key[i] >= 0) ++cnt;
+      }
+      // a warp inside one long row (a hub's) adds once for all its lanes
+      const int64_t cur0 = __shfl_sync(0xffffffffu, cur, 0);
+      if (__all_sync(0xffffffffu, groups == 1 && cur == cur0)) {
+        const unsigned tot = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0) {
+          if (MODE == 0) atomicAdd(&deg[cur0], (int)tot);
+          else atomicAdd(&dplus[cur0], (unsigned long long)tot);
+        }
+      } else if (cur >= 0) {
+        if (MODE == 0) atomicAdd(&deg[cur], (int)cnt);
+        else atomicAdd(&dplus[cur], (unsigned long long)cnt);
+      }
+    } else {
+      int64_t cur = -1, pos = 0;
+#pragma unroll
+      for (int i = 0; i < SP_ITEMS; ++i) {
+        if (key[i] >= 0) {
+          if (key[i] != cur) {  // first item of a group: reserve the group's slots
+            cur = key[i];
+            unsigned c = 0;
+#pragma unroll
+            for (int j = i; j < SP_ITEMS; ++j) c += key[j] == cur ? 1u : 0u;
+            pos = rowptr_o[cur] + (int64_t)atomicAdd(&cursor[cur], c);
+          }
+          colidx_o[pos] = val[i];
+          esrc_o[pos] = (int32_t)cur;
+          ++pos;
         }
       }
     }
@@ -454,10 +491,50 @@ __device__ __forceinline__ void sort_row_regs(int32_t *__restrict__ row, int len
   }
 }
 
-// Sort every oriented row ascending: one warp per row. Rows of up to 1024 are
-// sorted in registers (bitonic network over shuffles and register slots,
-// padded to 32 * 2^t), longer rows (up to SEG_CAP) in the warp's shared memory.
+// Bitonic network over W values held by one thread (all indices are
+// compile-time constants, so the values stay in registers).
+template <int W>
+__device__ __forceinline__ void thread_bitonic(int32_t (&x)[W]) {
+#pragma unroll
+  for (int k = 2; k <= W; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int32_t a = x[i], b = x[l];
+          if ((i & k) == 0) {
+            x[i] = min(a, b);
+            x[l] = max(a, b);
+          } else {
+            x[i] = max(a, b);
+            x[l] = min(a, b);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void sort_row_thread(int32_t *__restrict__ row, int len) {
+  int32_t x[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) x[i] = i < len ? row[i] : INT_MAX;
+  thread_bitonic<W>(x);
+#pragma unroll
+  for (int i = 0; i < W; ++i)
+    if (i < len) row[i] = x[i];
+}
+
+// Sort every oriented row ascending. A warp takes 32 rows at a time: each
+// lane sorts its own row when it has at most 16 entries (a register network
+// of 8 or 16), then the warp sorts the longer rows one at a time: up to 1024
+// in registers (bitonic network over shuffles and register slots, padded to
+// 32 * 2^t), longer ones (up to SEG_CAP) in the warp's shared memory.
 constexpr int SR_WARPS = 4;
+constexpr int SR_SMALL = 16;
 
 __global__ void __launch_bounds__(SR_WARPS * 32) k_sort_rows(const int64_t *__restrict__ rowptr,
                                                              int64_t n,
@@ -466,46 +543,69 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_sort_rows(const int64_t *__re
   const unsigned lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
   int32_t *sm = buf[warp];
+  // rows are dealt round-robin over the warps (row r to warp r mod W), so that
+  // runs of long rows, which the degree order keeps together, spread evenly
   const int64_t nwarps = (int64_t)gridDim.x * SR_WARPS;
-  for (int64_t r = (int64_t)blockIdx.x * SR_WARPS + warp; r < n; r += nwarps) {
-    const int64_t b = rowptr[r];
-    const int len = (int)(rowptr[r + 1] - b);
-    if (len <= 1) continue;
-    int32_t *row = colidx + b;
-    if (len <= 32) {
-      sort_row_regs<1>(row, len, lane);
-    } else if (len <= 64) {
-      sort_row_regs<2>(row, len, lane);
-    } else if (len <= 128) {
-      sort_row_regs<4>(row, len, lane);
-    } else if (len <= 256) {
-      sort_row_regs<8>(row, len, lane);
-    } else if (len <= 512) {
-      sort_row_regs<16>(row, len, lane);
-    } else if (len <= 1024) {
-      sort_row_regs<32>(row, len, lane);
-    } else {
-      int size = 64;
-      while (size < len) size <<= 1;
-      for (int i = lane; i < size; i += 32) sm[i] = i < len ? row[i] : INT_MAX;
-      __syncwarp();
-      for (int k = 2; k <= size; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int i = lane; i < size; i += 32) {
-            const int l = i ^ j;
-            if (l > i) {
-              const int32_t a = sm[i], c = sm[l];
-              const bool up = (i & k) == 0;
-              if ((a > c) == up) {
-                sm[i] = c;
-                sm[l] = a;
+  const int64_t gw = (int64_t)blockIdx.x * SR_WARPS + warp;
+  for (int64_t t0 = 0; gw + nwarps * t0 < n; t0 += 32) {
+    const int64_t r = gw + nwarps * (t0 + lane);
+    int64_t b = 0;
+    int len = 0;
+    if (r < n) {
+      b = rowptr[r];
+      len = (int)(rowptr[r + 1] - b);
+    }
+    const bool small = len > 1 && len <= SR_SMALL;
+    const int small_max = __reduce_max_sync(0xffffffffu, small ? len : 0);
+    if (small_max > 0) {
+      if (small_max <= 8) {
+        if (small) sort_row_thread<8>(colidx + b, len);
+      } else {
+        if (small) sort_row_thread<16>(colidx + b, len);
+      }
+    }
+    unsigned big = __ballot_sync(0xffffffffu, len > SR_SMALL);
+    while (big) {
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const int64_t bb = __shfl_sync(0xffffffffu, b, src);
+      const int blen = __shfl_sync(0xffffffffu, len, src);
+      int32_t *row = colidx + bb;
+      if (blen <= 32) {
+        sort_row_regs<1>(row, blen, lane);
+      } else if (blen <= 64) {
+        sort_row_regs<2>(row, blen, lane);
+      } else if (blen <= 128) {
+        sort_row_regs<4>(row, blen, lane);
+      } else if (blen <= 256) {
+        sort_row_regs<8>(row, blen, lane);
+      } else if (blen <= 512) {
+        sort_row_regs<16>(row, blen, lane);
+      } else if (blen <= 1024) {
+        sort_row_regs<32>(row, blen, lane);
+      } else {
+        int size = 64;
+        while (size < blen) size <<= 1;
+        for (int i = lane; i < size; i += 32) sm[i] = i < blen ? row[i] : INT_MAX;
+        __syncwarp();
+        for (int k = 2; k <= size; k <<= 1)
+          for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < size; i += 32) {
+              const int l = i ^ j;
+              if (l > i) {
+                const int32_t a = sm[i], c = sm[l];
+                const bool up = (i & k) == 0;
+                if ((a > c) == up) {
+                  sm[i] = c;
+                  sm[l] = a;
+                }
               }
             }
+            __syncwarp();
           }
-          __syncwarp();
-        }
-      for (int i = lane; i < len; i += 32) row[i] = sm[i];
-      __syncwarp();
+        for (int i = lane; i < blen; i += 32) row[i] = sm[i];
+        __syncwarp();
+      }
     }
   }
 }
@@ -613,7 +713,8 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   BBTC_LAUNCH_CHECK();
   if (m > 0) {
     if (g->dplus_max <= SEG_CAP) {
-      k_sort_rows<<<grid_for(n, SR_WARPS, 64), SR_WARPS * 32, 0, s>>>(g->rowptr, n, g->colidx);
+      k_sort_rows<<<grid_for((n + 31) / 32, SR_WARPS, 64), SR_WARPS * 32, 0, s>>>(g->rowptr, n,
+                                                                                g->colidx);
       BBTC_LAUNCH_CHECK();
     } else {
       uint64_t *ok = nullptr, *ok_alt = nullptr;

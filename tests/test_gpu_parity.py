@@ -299,3 +299,21 @@ def test_probe_partition_edge_cases():
     check_probe_partition(two_k64, (2, 3))
     # p = 64 (2048 grains) on an R-MAT graph of scale 12
     check_probe_partition(graphgen.rmat(12, 16, 9), (64,))
+
+
+def test_wide_lists_hash_and_sorted_staging():
+    """G(n,m) with n = 200,000 and 6 M pairs: degrees are near uniform, so the
+    degree order spreads each out-list over most positions above it. About 62%
+    of the probes go to lists whose value range is wider than the 65,536-bit
+    bitmap and which are longer than 16: AUTO and HASHMAP stage those as hash
+    tables; AUTO with a high threshold and INTERSECT stage them sorted. Every
+    staged form must give the oracle's per-task counts."""
+    n, rp, ci = graphgen.gnm(200000, 6000000, 78)
+    ref = oracle.prepare(n, rp, ci)
+    with bb.Graph(n, rp, ci, symmetric=True) as dev:
+        for p in (1, 4):
+            r = oracle.bbtc(n, rp, ci, p=p, prep=ref)
+            for kern, thr in (("auto", 0), ("hashmap", 0), ("auto", 1 << 20), ("intersect", 0)):
+                out = dev.count(p=p, kernel=kern, hash_threshold=thr, per_task=True)
+                assert out["total"] == r["total"] == 36183, (p, kern, thr)
+                assert np.array_equal(out["per_task"], r["per_task"]), (p, kern, thr)
