@@ -46,7 +46,7 @@ WORKLOADS = {
     "chunglu-friendster": "Friendster-shaped Chung-Lu: 65,608,366 vertices, 1,806,067,135 "
                           "pairs, degree exponent 2.1, expected degree capped at 5,000, seed 3",
 }
-DEFAULT_P = {"rmat-s23": 4, "rmat-s14": 2, "chunglu-friendster": 8}
+DEFAULT_P = {"rmat-s23": 4, "rmat-s14": 2, "chunglu-friendster": 1}
 WORKLOADS["batch-4096"] = ("4096 independent graphs (seeds 100-4195), pair counts log-uniform "
                            "in [1e3, 2e6]; even g: G(n,m) with average degree 8-64, odd g: "
                            "R-MAT a=.57 with edge factor 8-32")

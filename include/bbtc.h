@@ -75,7 +75,9 @@ typedef enum {
 
 typedef struct {
   uint32_t struct_size;         /* sizeof(bbtc_opts); set by bbtc_opts_init */
-  int32_t p;                    /* blocks per side, 1 <= p <= 64; 0 = choose from the graph */
+  int32_t p;                    /* blocks per side, 1 <= p <= 64; 0 = choose from the graph
+                                   (resident: 1 below 65,536 edges, else 2; under a device
+                                   budget: 2, 4 or 8 as m grows) */
   int32_t kernel;               /* bbtc_kernel */
   uint32_t timeout_ms;          /* 0 = no limit on the counting kernel's bounded waits */
   uint64_t device_budget_bytes; /* 0 = blocks resident; else the counting step keeps at most

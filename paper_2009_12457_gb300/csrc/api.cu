@@ -353,9 +353,9 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   bbtc_opts opts;
   BBTC_TRY(check_opts(opts_in, &opts));
   DeviceGuard dg(g->device);
-  const int p = opts.p == 0 ? default_p(g) : opts.p;
-  cudaStream_t s = opts.stream ? (cudaStream_t)opts.stream : g->stream;
   const bool budgeted = opts.device_budget_bytes != 0;
+  const int p = opts.p == 0 ? default_p(g, budgeted) : opts.p;
+  cudaStream_t s = opts.stream ? (cudaStream_t)opts.stream : g->stream;
   if (budgeted && opts.per_edge_out) {
     set_error("bbtc_count: per_edge_out needs a resident count (device_budget_bytes = 0)");
     return BBTC_EINVAL;

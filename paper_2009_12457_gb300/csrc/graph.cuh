@@ -219,8 +219,8 @@ bbtc_status wedge_sums(const bbtc_graph *g, uint64_t *in_sum, uint64_t *out_sum,
 // bbtc_count_batch. The caller destroys the union.
 bbtc_status union_of(const bbtc_graph_t *gs, int32_t ng, cudaStream_t s, bbtc_graph **out);
 
-// Default p when the caller passes 0 (Sec. 7.3: p near the average degree,
-// clamped for a single resident GPU).
-int default_p(const bbtc_graph *g);
+// Default p when the caller passes 0: small for resident counts, growing with
+// m when blocks stream under a device budget.
+int default_p(const bbtc_graph *g, bool budgeted = false);
 
 }  // namespace bbtc

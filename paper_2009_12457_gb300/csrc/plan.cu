@@ -376,11 +376,15 @@ void free_plan(Plan *pl, cudaStream_t s) {
   *pl = Plan();
 }
 
-int default_p(const bbtc_graph *g) {
-  // Sec. 7.3 suggests p near the average degree for a CPU cache; on one GPU
-  // with the whole graph resident, fewer and larger blocks keep the per-task
-  // overheads small. Grow p slowly with m.
+int default_p(const bbtc_graph *g, bool budgeted) {
+  // Sec. 7.3 suggests p near the average degree for a CPU cache. On one GPU with
+  // the whole graph resident nothing needs small blocks: fewer parts stage each
+  // N(G_jk, v) once and probe it in longer runs (on the Friendster-shaped graph
+  // the count takes 293 ms at p = 1, 472 ms at p = 8 and 654 ms at p = 16), so
+  // resident counts take 2 parts (1 for small graphs). Under a device budget a
+  // task's three blocks must fit in half the budget: p grows with m.
   if (g->m < (1 << 16)) return 1;
+  if (!budgeted) return 2;
   if (g->m < (1 << 22)) return 2;
   if (g->m < (1 << 27)) return 4;
   return 8;
