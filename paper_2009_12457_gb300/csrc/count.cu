@@ -55,11 +55,25 @@ static_assert(STAGE % 4 == 0, "the bitmap is cleared with 16-byte stores");
 constexpr int STAGE_POW2 = STAGE >= 2048 ? 2048 : STAGE >= 1024 ? 1024 : STAGE >= 512 ? 512 : 256;
 static_assert(STAGE_POW2 <= STAGE && STAGE >= 256, "stage too small");
 constexpr int MIN_STAGE = 8;
-constexpr int ST_NONE = 0, ST_SORTED = 1, ST_HASH = 2, ST_BITMAP = 3;
+constexpr int ST_NONE = 0, ST_SORTED = 1, ST_HASH = 2, ST_BITMAP = 3, ST_FILTER = 4;
+// ST_FILTER: an open-addressed table of up to FILTER_SLOTS slots in the upper
+// half of the stage, with a bit filter over a second hash of the keys in the
+// lower half. A probe reads one filter word and looks in the table only when
+// its bit is set: for a key not in the list that happens with probability at
+// most blen / FILTER_BITS (below 1/64 for blen <= 512).
+constexpr int FILTER_WORDS = STAGE / 2;
+constexpr int FILTER_BITS_LOG2 = 15;
+constexpr int FILTER_SLOTS = STAGE - FILTER_WORDS;
+static_assert(FILTER_WORDS * 32 == 1 << FILTER_BITS_LOG2, "filter size");
+static_assert((FILTER_SLOTS & (FILTER_SLOTS - 1)) == 0 && FILTER_WORDS % 4 == 0, "filter table");
 constexpr int32_t EMPTY = -1;
 
 __device__ __forceinline__ uint32_t hash_slot(int32_t w, int log2h) {
   return ((uint32_t)w * 2654435761u) >> (32 - log2h);
+}
+
+__device__ __forceinline__ uint32_t filter_bit(int32_t w) {
+  return ((uint32_t)w * 0x85EBCA6Bu) >> (32 - FILTER_BITS_LOG2);
 }
 
 // Membership of w in the sorted list stage[0, len): lower bound by a fixed
@@ -86,6 +100,18 @@ __device__ __forceinline__ bool hash_contains(const int32_t *stage, int log2h, i
     g = (g + 1) & gmask;
   }
   return false;
+}
+
+// The table half of an ST_FILTER stage, reached only when the filter bit is set.
+__device__ __forceinline__ bool filter_verify(const int32_t *table, int log2h, int32_t w) {
+  return hash_contains(table, log2h, w);
+}
+
+__device__ __forceinline__ uint32_t filter_lookup(const int32_t *stage, int log2h, int32_t w) {
+  const uint32_t h = filter_bit(w);
+  const uint32_t word = reinterpret_cast<const uint32_t *>(stage)[h >> 5];
+  if (((word >> (h & 31u)) & 1u) == 0u) return 0u;
+  return filter_verify(stage + FILTER_WORDS, log2h, w) ? 1u : 0u;
 }
 
 // Per-batch lane records, shared by the warp: where each in-edge's probes
@@ -367,6 +393,8 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
             if (blen <= STAGE) mode = ST_SORTED;
           } else if (span <= (int64_t)STAGE * 32) {
             mode = ST_BITMAP;
+          } else if (2 * blen <= FILTER_SLOTS && (kflag == 1 || blen > hash_min)) {
+            mode = ST_FILTER;
           } else if (2 * blen <= STAGE_POW2 && (kflag == 1 || blen > hash_min)) {
             mode = ST_HASH;
           } else if (kflag == 2 && blen <= STAGE) {
@@ -385,6 +413,28 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
               }
               staged_first = first;
               staged_len = (int)span;
+            } else if (mode == ST_FILTER) {
+              int log2h = 5;
+              while ((1 << log2h) < 2 * blen) ++log2h;
+              const int hsize = 1 << log2h;
+              int4 *f4 = reinterpret_cast<int4 *>(stage);
+              for (int i = lane; i < FILTER_WORDS / 4; i += 32) f4[i] = make_int4(0, 0, 0, 0);
+              int32_t *table = stage + FILTER_WORDS;
+              for (int i = lane; i < hsize; i += 32) table[i] = EMPTY;
+              __syncwarp();
+              const uint32_t hmask = (uint32_t)hsize - 1u;
+              for (int i = lane; i < blen; i += 32) {
+                const int32_t key = ci_jk[b0 + i];
+                const uint32_t fb = filter_bit(key);
+                atomicOr(reinterpret_cast<unsigned *>(stage) + (fb >> 5), 1u << (fb & 31u));
+                uint32_t h = hash_slot(key, log2h) & ~3u;
+                for (int n = 0; n < hsize; ++n) {
+                  if (atomicCAS(&table[h], EMPTY, key) == EMPTY) break;
+                  h = (h + 1) & hmask;
+                }
+              }
+              staged_log2h = log2h;
+              staged_len = blen;
             } else if (mode == ST_HASH) {
               int log2h = 5;
               while ((1 << log2h) < 2 * blen) ++log2h;
@@ -416,9 +466,10 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         }
       }
 
-      if (MODE == 0 && staged && staged_mode == ST_BITMAP) {
-        // quad probes (see probe_quads); hash-table and sorted lookups keep the
-        // single-probe loop below, which measured faster for them
+      if (MODE == 0 && staged && (staged_mode == ST_BITMAP || staged_mode == ST_FILTER)) {
+        // quad probes (see probe_quads) against a bitmap or a filtered table;
+        // plain hash-table and sorted lookups keep the single-probe loop below,
+        // which measured faster for them
         const uint32_t a0 = (uint32_t)s0 & ~3u;
         const uint32_t nq = len ? ((uint32_t)s1 - a0 + 3u) >> 2 : 0u;
         const uint32_t inclq = warp_inclusive_scan(nq);
@@ -427,14 +478,21 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         rec.s1[lane] = (uint32_t)s1;
         rec.incl[lane] = inclq;
         __syncwarp();
-        const unsigned *__restrict__ bm = reinterpret_cast<const unsigned *>(stage);
-        const int32_t first = staged_first;
-        acc += probe_quads<2>(ci_ik, rec, totalq, lane, [&](int32_t w) -> uint32_t {
-          const uint32_t dlt = (uint32_t)(w - first);
-          // values outside [first, first + STAGE * 32) read the zero guard word
-          const uint32_t word = bm[min(dlt >> 5, (uint32_t)STAGE)];
-          return (word >> (dlt & 31u)) & 1u;
-        });
+        if (staged_mode == ST_BITMAP) {
+          const unsigned *__restrict__ bm = reinterpret_cast<const unsigned *>(stage);
+          const int32_t first = staged_first;
+          acc += probe_quads<2>(ci_ik, rec, totalq, lane, [&](int32_t w) -> uint32_t {
+            const uint32_t dlt = (uint32_t)(w - first);
+            // values outside [first, first + STAGE * 32) read the zero guard word
+            const uint32_t word = bm[min(dlt >> 5, (uint32_t)STAGE)];
+            return (word >> (dlt & 31u)) & 1u;
+          });
+        } else {
+          const int log2h = staged_log2h;
+          acc += probe_quads<2>(ci_ik, rec, totalq, lane, [&](int32_t w) -> uint32_t {
+            return filter_lookup(stage, log2h, w);
+          });
+        }
         __syncwarp();
         continue;
       }
@@ -491,6 +549,10 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
           const uint32_t word = bm[min(dlt >> 5, (uint32_t)(STAGE - 1))];
           return ((dlt < span) & (word >> (dlt & 31u))) & 1u;
         });
+      } else if (staged && staged_mode == ST_FILTER) {
+        const int log2h = staged_log2h;
+        probe_batch<4>(ci_ik, rec, total, lane, on_hit,
+                       [&](int32_t w, int) { return filter_lookup(stage, log2h, w) != 0u; });
       } else if (staged && staged_mode == ST_HASH) {
         const int log2h = staged_log2h;
         probe_batch<4>(ci_ik, rec, total, lane, on_hit,
