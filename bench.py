@@ -65,6 +65,12 @@ def make_graph(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def step_stats(values):
+    """[median, min, p90] of per-step times (the paper reports medians of 5 runs)."""
+    v = sorted(values)
+    return [statistics.median(v), v[0], v[min(len(v) - 1, int(math.ceil(0.9 * len(v))) - 1)]]
+
+
 def reduce_max_ms(ms: float, dist, device) -> float:
     """Slowest rank's time: the job is done when every replica is."""
     if dist is None:
@@ -638,6 +644,9 @@ def main():
                     "parallelism": "replicas" if world > 1 else "single GPU",
                     "phase_ms": {"prep": statistics.mean(prep_ms), "plan": statistics.mean(plan_ms),
                                  "count_kernel": kms},
+                    "phase_ms_median_min_p90": {k: step_stats(v) for k, v in
+                                                (("prep", prep_ms), ("plan", plan_ms),
+                                                 ("count_kernel", count_ms))},
                     "device_budget_gb": budget_gb,
                     "streaming": dict(stream_info[-1], pinned_h2d_gbs=h2d_gbs) if budget else None,
                 },

@@ -191,6 +191,9 @@ def test_invalid_inputs_are_rejected():
             dev.count(p=65)
         with pytest.raises(bb.BbtcError):
             dev.count(p=-1)
+        with pytest.raises(bb.BbtcError) as e:
+            dev.count(p=2, partition=2)                # not a bbtc_partition
+        assert e.value.status == 1
         assert dev.count(p=2) == 4  # the handle still works after a rejected call
 
 
