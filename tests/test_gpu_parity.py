@@ -320,3 +320,8 @@ def test_wide_lists_hash_and_sorted_staging():
                 out = dev.count(p=p, kernel=kern, hash_threshold=thr, per_task=True)
                 assert out["total"] == r["total"] == 36183, (p, kern, thr)
                 assert np.array_equal(out["per_task"], r["per_task"]), (p, kern, thr)
+        # per-vertex counts take the single-probe loop through the same staged forms
+        pv_ref = oracle.per_vertex(n, ref["rowptr"], ref["colidx"], ref["perm"])
+        for kern in ("auto", "hashmap"):
+            out = dev.count(p=2, kernel=kern, per_vertex=True)
+            assert np.array_equal(out["per_vertex"], pv_ref), kern
