@@ -621,6 +621,10 @@ def main():
             # records (u, v, position), each N(v) staged once, and the part of each
             # N(u) above v (sum over u of d+(u)(d+(u)-1)/2 elements)
             own = 4 * (4 * m + info["wedges_out"])
+            # bytes a merge-based intersection of both full lists would read:
+            # 4 * sum over (u,v) of (d+(u) + d+(v)), with sum_(u,v) d+(u) = sum_u d+(u)^2
+            # = 2 * sum_u C(d+(u), 2) + m
+            wmerge = 4 * (2 * info["wedges_out"] + m + info["wedges_in"])
             h2d = (n + 1) * 8 + int(h_ci.numel()) * 4
             line = {
                 "metric": METRIC,
@@ -663,6 +667,7 @@ def main():
                              "kernel_own_bytes": own,
                              "kernel_own_formula": "4*(4m + sum over u of d+(u)(d+(u)-1)/2)",
                              "kernel_own_frac": own / (kms / 1000.0) / 1e9 / peak,
+                             "w_merge_bytes": wmerge,
                              "peak_source": f"{peak_kind} hbm_gbs"},
                 "clocks": clocks.summary(),
                 "gpu_launches": launches,
