@@ -65,3 +65,25 @@ def test_argument_errors_without_touching_the_gpu():
 def test_python_binding_rejects_bad_dtypes():
     with pytest.raises(TypeError):
         bb.bbtc_graph_create(2, np.zeros(3, dtype=np.int32), np.zeros(0, dtype=np.int32))
+
+
+def _c_struct_fields(name):
+    """Field names of a typedef'd struct in include/bbtc.h, in declaration order."""
+    text = open(os.path.join(ROOT, "include", "bbtc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text).group(1)
+    return re.findall(r"([A-Za-z_][A-Za-z0-9_]*)\s*;", body)
+
+
+def test_python_structs_mirror_the_header():
+    assert [f for f, _ in bb.bbtc_opts._fields_] == _c_struct_fields("bbtc_opts")
+    assert [f for f, _ in bb.bbtc_graph_info._fields_] == _c_struct_fields("bbtc_graph_info")
+    assert [f for f, _ in bb.bbtc_timings._fields_] == _c_struct_fields("bbtc_timings")
+
+
+def test_partition_option():
+    assert bb.bbtc_opts_init().partition == 0           # edge-balanced by default
+    assert bb.make_opts(p=4, partition="probe").partition == 1
+    assert bb.make_opts(p=4, partition="edges").partition == 0
+    text = open(os.path.join(ROOT, "include", "bbtc.h")).read()
+    assert "BBTC_PARTITION_EDGES = 0" in text and "BBTC_PARTITION_PROBE = 1" in text
