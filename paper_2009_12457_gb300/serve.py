@@ -140,6 +140,11 @@ class Server:
         ent.ready.set()
         return ent
 
+    def _note_error(self, exc):
+        with self.cv:
+            if len(self.errors) < 16:
+                self.errors.append(f"{type(exc).__name__}: {exc}")
+
     def _release(self, key):
         with self.cv:
             ent = self.cache.get(key)
@@ -166,14 +171,19 @@ class Server:
                 with torch.cuda.stream(stream):
                     handles = []
                     for r in batch:
-                        handles.append(self._acquire(r.key, stream).handle)
-                        acquired.append(r.key)
+                        # a graph that cannot be prepared fails its own request only:
+                        # its slot goes to the batch count as NULL, which the library
+                        # reports per graph while it counts the others
+                        try:
+                            handles.append(self._acquire(r.key, stream).handle)
+                            acquired.append(r.key)
+                        except Exception as exc:
+                            self._note_error(exc)
+                            handles.append(None)
                     opts = make_opts(p=self.p, kernel=self.kernel, stream=stream)
                     counts, stats = bbtc_count_batch(handles, opts)
-            except Exception as exc:  # the batch fails as a whole; the server keeps running
-                with self.cv:
-                    if len(self.errors) < 16:
-                        self.errors.append(f"{type(exc).__name__}: {exc}")
+            except Exception as exc:  # the count failed: the batch fails, the server keeps running
+                self._note_error(exc)
                 counts = np.zeros(len(batch), dtype=np.uint64)
                 stats = np.full(len(batch), 6, dtype=np.int32)
             t1 = time.perf_counter()

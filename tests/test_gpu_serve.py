@@ -1,4 +1,6 @@
 """Serving loop: each request's count is the same alone and in the mix (GPU)."""
+import time
+
 import numpy as np
 import pytest
 
@@ -72,3 +74,43 @@ def test_autotuner_choice_gives_the_same_count(tmp_path):
     again = Autotuner(cache_path=str(tmp_path / "tune.json"))
     with bb.Graph(n, rp, ci) as g:
         assert again.choice(g, tune_if_missing=False)["p"] == choice["p"]
+
+
+def test_a_bad_graph_fails_only_its_own_requests():
+    """A request whose graph cannot be prepared (an out-of-range column) fails with
+    its own status; the requests that share its batch are still counted, and the
+    server keeps serving."""
+    bad_rp = np.array([0, 1, 2], dtype=np.int64)
+    bad_ci = np.array([1, 5], dtype=np.int32)      # 5 is outside [0, 2)
+
+    def mixed_source(key):
+        return (2, bad_rp, bad_ci) if key == "bad" else source(key)
+
+    good = [request_key(i) for i in range(40)]
+    keys = good[:20] + ["bad"] + good[20:] + ["bad"]
+    alone = {}
+    for k in set(good):
+        with bb.Graph(*source(k)) as g:
+            alone[k] = g.count(p=2)
+    srv = serve.Server(mixed_source, device_budget_bytes=1 << 30, max_batch=64, workers=1, p=2)
+    try:
+        reqs = [serve.Request(i, k, time.perf_counter()) for i, k in enumerate(keys)]
+        with srv.cv:  # the worker takes the whole burst as one batch
+            for r in reqs:
+                srv.submit(r)
+        srv.drain(len(reqs))
+        later = [serve.Request(len(keys) + i, k, time.perf_counter())
+                 for i, k in enumerate(good[:5])]
+        for r in later:                              # still serving
+            srv.submit(r)
+        srv.drain(len(reqs) + len(later))
+    finally:
+        srv.close()
+    for r in reqs:
+        if r.key == "bad":
+            assert r.status != 0
+        else:
+            assert r.status == 0 and r.count == alone[r.key], (r.key, r.status, r.count)
+    assert all(r.batch_size == len(keys) for r in reqs)   # the bad graphs shared the batch
+    assert srv.errors
+    assert all(r.status == 0 and r.count == alone[r.key] for r in later)
