@@ -88,6 +88,38 @@ def per_task_brute(n, rowptr, colidx, p):
     return out
 
 
+def position_adjacency(A, rank):
+    """Dense adjacency in position space with every edge stored once, u < v (Sec. 2)."""
+    Ar = np.zeros_like(A)
+    ar, br = np.nonzero(np.triu(A, 1))
+    Ar[np.minimum(rank[ar], rank[br]), np.maximum(rank[ar], rank[br])] = 1
+    return Ar
+
+
+def block_nnz_by_definition(Ar, c):
+    """|G_ij| = edges (u, v), u < v, with u in V_i = [c_i, c_{i+1}) and v in V_j (Sec. 2),
+    summed over the dense position-space adjacency; empty parts hold nothing."""
+    p = len(c) - 1
+    out = np.zeros((p, p), dtype=np.int64)
+    for i in range(p):
+        for j in range(p):
+            out[i, j] = int(Ar[c[i]:c[i + 1], c[j]:c[j + 1]].sum())
+    return out
+
+
+def cuts_with_empty_parts(n, p, rng):
+    """Random valid cuts c_0 = 0 <= ... <= c_p = n in which some parts are empty:
+    the first, the last and one in the middle (when p allows)."""
+    inner = np.sort(rng.integers(0, n + 1, p - 1)) if p > 1 else np.array([], dtype=np.int64)
+    c = np.concatenate([[0], inner, [n]]).astype(np.int64)
+    if p >= 2:
+        c[1] = 0                     # part 0 empty
+        c[p - 1] = n                 # part p-1 empty
+    if p >= 4:
+        c[2] = c[3]                  # part 2 empty
+    return np.maximum.accumulate(c)
+
+
 def with_noise(n, rowptr, colidx, rng, dup=0.3, loops=3):
     """Same simple graph, with duplicate entries and self-loops added."""
     rows = [list(colidx[rowptr[v]:rowptr[v + 1]]) for v in range(n)]
@@ -243,6 +275,14 @@ def pin_battery() -> list[str]:
         A, deg, rank, perm, outdeg = positions_by_definition(*g)
         check(np.array_equal(pr["perm"], perm), f"degree order trial {trial}")
         check(np.array_equal(np.diff(pr["rowptr"]), outdeg), f"out-degrees trial {trial}")
+        # |G_ij| (Sec. 2) for the whole p x p matrix, against the dense adjacency:
+        # on the edge-balanced cuts and on cuts with empty parts
+        Ar = position_adjacency(A, rank)
+        for p in (1, 2, 3, 5, 8):
+            for c in (cuts_by_definition(n, outdeg, p), cuts_with_empty_parts(n, p, rng)):
+                got = oracle.block_nnz(n, pr["rowptr"], pr["colidx"], p, c)
+                check(np.array_equal(got, block_nnz_by_definition(Ar, c)),
+                      f"block sizes p={p} cuts {c.tolist()} trial {trial}")
         for p in (1, 2, 3, 5):
             c = oracle.cuts(n, pr["rowptr"], p)
             check(np.array_equal(c, cuts_by_definition(n, outdeg, p)), f"cuts p={p} trial {trial}")
@@ -272,11 +312,24 @@ def pin_battery() -> list[str]:
     order = oracle.order_tasks(np.array([1.0, 3.0, 3.0, 2.0]))
     check(order.tolist() == [1, 2, 3, 0], "task order: non-increasing, ties in Alg.4 order")
 
-    # algorithmic-bytes figures on a path a-b-c plus triangle: by hand
+    # algorithmic-bytes figures on the triangle 0-1-2 with a pendant vertex 3 on 2,
+    # by hand: degrees 2, 2, 3, 1 give the order 3, 0, 1, 2 (positions 0..3), the
+    # oriented edges (0,3), (1,2), (1,3), (2,3) and out-degrees d+ = 1, 2, 1, 0.
+    # wedges = sum over edges of d+(v) = 0 + 1 + 0 + 0 = 1; wmin = 4 * (4 + 1) = 20;
+    # wmerge = 4 * sum over edges of (d+(u) + d+(v)) = 4 * (1 + 3 + 2 + 1) = 28.
     n, rp, ci = G.csr_from_edges(4, [(0, 1), (1, 2), (0, 2), (2, 3)])
     pr = oracle.prepare(n, rp, ci)
     wf = oracle.work_figures(n, pr["rowptr"], pr["colidx"])
-    d = np.diff(pr["rowptr"])
-    wedges = sum(int(d[v]) for u in range(n) for v in pr["colidx"][pr["rowptr"][u]:pr["rowptr"][u + 1]])
-    check(wf["wedges"] == wedges and wf["wmin"] == 4 * (4 + wedges), "work figures")
+    check((wf["wedges"], wf["wmin"], wf["wmerge"]) == (1, 20, 28), f"work figures by hand {wf}")
+    # and on random graphs, from the dense position-space adjacency
+    for trial in range(4):
+        nn = int(rng.integers(8, 40))
+        g = G.gnp(nn, float(rng.uniform(0.1, 0.6)), rng)
+        A, deg, rank, perm, outdeg = positions_by_definition(*g)
+        us, vs = np.nonzero(position_adjacency(A, rank))
+        pr = oracle.prepare(*g)
+        wf = oracle.work_figures(nn, pr["rowptr"], pr["colidx"])
+        want = (int(outdeg[vs].sum()), 4 * (len(us) + int(outdeg[vs].sum())),
+                4 * int((outdeg[us] + outdeg[vs]).sum()))
+        check((wf["wedges"], wf["wmin"], wf["wmerge"]) == want, f"work figures trial {trial}")
     return fails

@@ -52,6 +52,13 @@ MUTANTS = {
     "pbd_probe_not_greedy": ("      best = t;\n    }", "      best = t;\n      break;\n    }"),
     "pbd_bisection_keeps_lo": ("if (orc_pbd_probe(G, S, p, mid, x)) hi = mid; else lo = mid;",
                                "if (orc_pbd_probe(G, S, p, mid, x)) lo = mid; else hi = mid;"),
+    # |G_ij| stored at (j, i): the largest block is unchanged, the matrix is not
+    "block_nnz_transposed": ("nnz[(int64_t)i * p + part_of(ci[e], p, cuts)] += 1;",
+                             "nnz[(int64_t)part_of(ci[e], p, cuts) * p + i] += 1;"),
+    # a position after an empty part is given to that empty part
+    "part_of_stops_at_empty_part": ("while (i + 1 < p && cuts[i + 1] <= r) ++i;",
+                                    "while (i + 1 < p && cuts[i + 1] <= r && cuts[i + 1] > cuts[i]) ++i;"),
+    "wmerge_counts_v_twice": ("mg += du + dv;", "mg += dv + dv;"),
     "classify_drops_w_part": ("per_task[idx[((int64_t)bu * p + bv) * p + part_of(ci[a], p, cuts)]] += 1;",
                               "per_task[idx[((int64_t)bu * p + bv) * p + bv]] += 1;"),
 }
