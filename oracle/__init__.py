@@ -127,12 +127,17 @@ def _c(a, dtype):
 
 # ------------------------------------------------------------------- steps
 
-def canonical_edges(n: int, rowptr, colidx) -> np.ndarray:
-    """Sorted unique keys (a << 32) | b, a < b, of the simple undirected edge set."""
+def canonical_edges(n: int, rowptr, colidx, compact: bool = True) -> np.ndarray:
+    """Sorted unique keys (a << 32) | b, a < b, of the simple undirected edge set.
+
+    compact=False returns a view into the rowptr[n]-entry work buffer instead of
+    a copy of its first m entries (the caller then decides when to copy, e.g.
+    after freeing the input of a graph too large to hold twice).
+    """
     rowptr, colidx = _c(rowptr, np.int64), _c(colidx, np.int32)
     keys = np.empty(max(int(rowptr[n]), 1), dtype=np.uint64)
     m = _load().orc_canonical_edges(n, _p(rowptr), _p(colidx), _p(keys))
-    return keys[:m].copy()
+    return keys[:m].copy() if compact else keys[:m]
 
 
 def degree(n: int, keys) -> np.ndarray:
