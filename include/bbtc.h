@@ -238,13 +238,16 @@ bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts
  *
  *   p             1..16: the fixed array holds at most 816 task counters
  *   count_dev     DEVICE pointer to one uint64: the total
- *   per_task_dev  NULL, or DEVICE pointer to bbtc_num_tasks(p) uint64 in Alg. 4 order
+ *   per_task_dev  NULL, or DEVICE pointer to bbtc_num_tasks(p) uint64, in the same task
+ *                 order as bbtc_count's per_task_out
  *   stream        cudaStream_t (NULL = the handle's stream); the call is
  *                 asynchronous: outputs are ready when the stream reaches them
  *
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. Every call shares the one array and it keeps the last call's
+ * device, with that device current, guarded so that concurrent first calls
+ * from several host threads are safe); make that first call before any stream
+ * capture. A failed look-up is remembered and every later call on that device
+ * returns ECUDA. Every call shares the one array and it keeps the last call's
  * contents: each call clears what it needs, but calls whose work overlaps on
  * the GPU (other streams, other host threads) race on it and must be ordered
  * by the caller.
@@ -306,9 +309,30 @@ typedef struct {
   int64_t stream_rounds;      /* last budgeted count: rounds of block copies */
   uint64_t stream_h2d_bytes;  /* last budgeted count: block bytes copied to the device */
   double stream_copy_ms;      /* last budgeted count: device time of those copies */
+  uint64_t stream_block_bytes;  /* last budgeted count: bytes of all the plan's streamed
+                                   blocks (each block once) */
+  uint64_t stream_device_peak_bytes; /* last budgeted count: high-water mark of the library's
+                                        device memory during the count (the handle's
+                                        oriented CSR and plan tables, which stay resident,
+                                        plus the block pool of at most the budget) */
+  int32_t stream_mode;        /* last budgeted count: 1 = every block CSR kept on the device
+                                 and each in-edge block copied once; 2 = blocks placed round
+                                 by round in the pool and re-copied when evicted */
 } bbtc_timings;
 
 bbtc_status bbtc_graph_get_timings(bbtc_graph_t g, bbtc_timings *t);
+
+/*
+ * Device memory the library can still use on `device` (an ordinal): the free
+ * bytes the driver reports plus the bytes that the device's stream-ordered
+ * pool holds without using them (the library allocates from that pool and
+ * keeps freed blocks there for later calls, so the driver's figure alone
+ * undercounts). Any output may be NULL. Used by callers that admit work by
+ * free device memory, such as the serving loop; the paper has no counterpart.
+ * Errors: EINVAL for an unknown device; ECUDA.
+ */
+bbtc_status bbtc_device_memory(int32_t device, uint64_t *available, uint64_t *total,
+                               uint64_t *pool_reserved, uint64_t *pool_used);
 
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t bbtc_kernel_launches(void);

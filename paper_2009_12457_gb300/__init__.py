@@ -23,7 +23,7 @@ __all__ = [
     "bbtc_count_batch", "bbtc_graph_plan", "bbtc_graph_destroy", "bbtc_last_error", "bbtc_num_tasks",
     "bbtc_opts_init", "bbtc_graph_get_info", "bbtc_graph_get_oriented", "bbtc_graph_get_plan",
     "bbtc_graph_get_timings", "bbtc_kernel_launches", "bbtc_count_noalloc",
-    "bbtc_graph_create_batch", "bbtc_count_async", "BatchGraph",
+    "bbtc_graph_create_batch", "bbtc_count_async", "bbtc_device_memory", "BatchGraph",
     "library_path", "load",
 ]
 
@@ -85,6 +85,9 @@ class bbtc_timings(ctypes.Structure):
         ("stream_rounds", ctypes.c_int64),
         ("stream_h2d_bytes", ctypes.c_uint64),
         ("stream_copy_ms", ctypes.c_double),
+        ("stream_block_bytes", ctypes.c_uint64),
+        ("stream_device_peak_bytes", ctypes.c_uint64),
+        ("stream_mode", ctypes.c_int32),
     ]
 
 
@@ -141,6 +144,8 @@ def load():
         lib.bbtc_graph_create_batch.restype = st
         lib.bbtc_count_async.argtypes = [P, ctypes.POINTER(bbtc_opts), P]
         lib.bbtc_count_async.restype = st
+        lib.bbtc_device_memory.argtypes = [i32, P, P, P, P]
+        lib.bbtc_device_memory.restype = st
         _lib = lib
         return lib
 
@@ -342,6 +347,17 @@ def bbtc_graph_get_timings(handle: int) -> dict:
 
 def bbtc_kernel_launches() -> int:
     return int(load().bbtc_kernel_launches())
+
+
+def bbtc_device_memory(device: int = 0) -> dict:
+    """Device memory the library can still use on `device` (driver free bytes plus
+    the unused part of its stream-ordered pool), with the total and the pool's
+    reserved and used bytes."""
+    out = np.zeros(4, dtype=np.uint64)
+    p = out.ctypes.data
+    _check(load().bbtc_device_memory(device, p, p + 8, p + 16, p + 24))
+    return {"available": int(out[0]), "total": int(out[1]), "pool_reserved": int(out[2]),
+            "pool_used": int(out[3])}
 
 
 # ------------------------------------------------------------- convenience

@@ -4,6 +4,7 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "graph.cuh"
@@ -13,7 +14,7 @@ namespace bbtc {
 
 namespace {
 thread_local char g_error[1024] = "";
-bool g_pool_ready[64] = {false};
+std::once_flag g_pool_once[64];
 unsigned long long g_launches = 0;
 }  // namespace
 
@@ -45,14 +46,14 @@ bbtc_status dalloc(void **p, size_t bytes, cudaStream_t s) {
     set_error("cudaGetDevice failed");
     return BBTC_ECUDA;
   }
-  if (dev >= 0 && dev < 64 && !g_pool_ready[dev]) {
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-      uint64_t threshold = ~0ull;  // keep freed blocks cached for the next call
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
-    }
-    g_pool_ready[dev] = true;
-  }
+  if (dev >= 0 && dev < 64)
+    std::call_once(g_pool_once[dev], [dev] {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t threshold = ~0ull;  // keep freed blocks cached for the next call
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+      }
+    });
   cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -391,6 +392,9 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
     g->stream_stats.rounds = st.rounds;
     g->stream_stats.h2d_bytes = st.h2d_bytes;
     g->stream_stats.copy_ms = st.copy_ms;
+    g->stream_stats.block_bytes = st.block_bytes;
+    g->stream_stats.device_peak = st.device_peak;
+    g->stream_stats.mode = st.mode;
     g->stream_stats_total_ms = st.total_ms;
   } else {
     BBTC_TRY(run_count(g, pl, vertex_count, per_graph, opts.timeout_ms, s, g->ev[4], g->ev[5],
@@ -400,10 +404,7 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
   unsigned long long head[SCR_TASKS] = {0, 0, 0};
   BBTC_CUDA(cudaMemcpyAsync(head, pl.scratch, sizeof(head), cudaMemcpyDeviceToHost, s));
   BBTC_CUDA(cudaStreamSynchronize(s));
-  if ((int32_t)head[SCR_STATUS] != 0) {
-    set_error("bbtc_count: the counting kernel passed its %u ms limit", opts.timeout_ms);
-    return BBTC_ETIMEOUT;
-  }
+  if ((int32_t)head[SCR_STATUS] != 0) return count_status_error("bbtc_count", (int32_t)head[SCR_STATUS], opts.timeout_ms);
   const bool out_dev = (opts.flags & BBTC_OUT_DEVICE) != 0;
   const cudaMemcpyKind kind = out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (opts.per_task_out)
@@ -600,6 +601,30 @@ bbtc_status bbtc_graph_get_info(bbtc_graph_t g, bbtc_graph_info *info) {
   return BBTC_OK;
 }
 
+bbtc_status bbtc_device_memory(int32_t device, uint64_t *available, uint64_t *total,
+                               uint64_t *pool_reserved, uint64_t *pool_used) {
+  clear_error();
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    set_error("bbtc_device_memory: no device %d", device);
+    return BBTC_EINVAL;
+  }
+  DeviceGuard dg(device);
+  size_t free_b = 0, total_b = 0;
+  BBTC_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  cudaMemPool_t pool;
+  BBTC_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+  uint64_t reserved = 0, used = 0;
+  BBTC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+  BBTC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  if (available) *available = (uint64_t)free_b + (reserved > used ? reserved - used : 0);
+  if (total) *total = (uint64_t)total_b;
+  if (pool_reserved) *pool_reserved = reserved;
+  if (pool_used) *pool_used = used;
+  return BBTC_OK;
+}
+
 bbtc_status bbtc_graph_get_timings(bbtc_graph_t g, bbtc_timings *t) {
   clear_error();
   if (!g || !t) {
@@ -623,6 +648,9 @@ bbtc_status bbtc_graph_get_timings(bbtc_graph_t g, bbtc_timings *t) {
   t->stream_rounds = g->stream_stats.rounds;
   t->stream_h2d_bytes = g->stream_stats.h2d_bytes;
   t->stream_copy_ms = g->stream_stats.copy_ms;
+  t->stream_block_bytes = g->stream_stats.block_bytes;
+  t->stream_device_peak_bytes = g->stream_stats.device_peak;
+  t->stream_mode = g->stream_stats.mode;
   return BBTC_OK;
 }
 

@@ -23,7 +23,8 @@ namespace bbtc {
 namespace {
 
 constexpr int CT_NT = 256;
-constexpr int MAXP = 64;
+
+constexpr int32_t STATUS_TIMEOUT = 1, STATUS_COPY_WAIT = 2;
 
 struct CountParams {
   const TaskDesc *desc;  // per task (Alg. 4 order): where its three blocks live
@@ -55,6 +56,8 @@ static_assert(STAGE % 4 == 0, "the bitmap is cleared with 16-byte stores");
 constexpr int STAGE_POW2 = STAGE >= 2048 ? 2048 : STAGE >= 1024 ? 1024 : STAGE >= 512 ? 512 : 256;
 static_assert(STAGE_POW2 <= STAGE && STAGE >= 256, "stage too small");
 constexpr int MIN_STAGE = 8;
+// lists at least this long are staged through one bulk copy (TMA)
+constexpr int BULK_STAGE_MIN = 64;
 constexpr int ST_NONE = 0, ST_SORTED = 1, ST_HASH = 2, ST_BITMAP = 3, ST_FILTER = 4;
 // ST_FILTER: an open-addressed table of up to FILTER_SLOTS slots in the upper
 // half of the stage, with a bit filter over a second hash of the keys in the
@@ -114,6 +117,87 @@ __device__ __forceinline__ uint32_t filter_lookup(const int32_t *stage, int log2
   return filter_verify(stage + FILTER_WORDS, log2h, w) ? 1u : 0u;
 }
 
+// ------------------------------------------------ bulk copies (TMA, PTX)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *m) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(m)) : "memory");
+}
+// Makes an initialised barrier visible to the bulk-copy unit.
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// The one arrival of the barrier's current phase, announcing `bytes` of copies.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *m, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(m)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// limit of one wait on a bulk copy (copies of valid addresses take microseconds)
+constexpr uint64_t COPY_WAIT_NS = 200ull * 1000 * 1000;
+// Waits for the barrier's phase of the given parity, for at most COPY_WAIT_NS.
+__device__ __noinline__ bool mbar_wait_bounded(unsigned long long *m, uint32_t parity) {
+  if (mbar_try_wait(m, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(m, parity))
+    if (global_ns() - t0 > COPY_WAIT_NS) return false;
+  return true;
+}
+// TMA bulk copy global -> shared of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned), completing on barrier m.
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes,
+                                          unsigned long long *m) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(m))
+      : "memory");
+}
+// Orders this thread's earlier plain shared-memory accesses before later bulk
+// copies into the same memory.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Starts one bulk copy of list[e0, e1) into `dst` (e0, e1 multiples of 4:
+// whole 16-byte quads of a 16-byte aligned, quad-padded column array; dst
+// 16-byte aligned), issued by lane 0 on barrier mbar. Warp-uniform call.
+__device__ __forceinline__ void bulk_issue(int32_t *dst, const int32_t *list, int64_t e0,
+                                           int64_t e1, unsigned long long *mbar, unsigned lane) {
+  fence_proxy_async();  // earlier plain accesses to the stage before the copy
+  __syncwarp();
+  if (lane == 0) {
+    const uint32_t bytes = (uint32_t)(4 * (e1 - e0));
+    mbar_expect_tx(mbar, bytes);
+    bulk_copy(dst, list + e0, bytes, mbar);
+  }
+}
+
+// Waits (bounded) for the copy of bulk_issue; true on every lane when it
+// arrived. On false the copy is awaited once more and the caller stops.
+__device__ __forceinline__ bool bulk_wait(unsigned long long *mbar, uint32_t &parity) {
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(mbar, parity));
+  if (!ok) {
+    mbar_wait_bounded(mbar, parity);
+    return false;
+  }
+  parity ^= 1u;
+  return true;
+}
+
 // Per-batch lane records, shared by the warp: where each in-edge's probes
 // start in the flattened probe sequence and where they come from.
 struct LaneRec {
@@ -124,6 +208,7 @@ struct LaneRec {
   uint32_t incl[32];  // inclusive prefix of the probe counts (quad counts for quad probes)
   int32_t u[32];
   int32_t v[32];
+  unsigned long long mbar;  // completion of bulk copies into the warp's stage
 };
 
 // Runs the flattened probes of one batch: probe q (0 <= q < total) belongs to
@@ -258,14 +343,22 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
   const unsigned lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
   int32_t *stage = reinterpret_cast<int32_t *>(count_smem_raw) + warp * (STAGE + 4);
-  if (lane == 0) stage[STAGE] = 0;  // guard word after the stage: always zero
   LaneRec &rec = reinterpret_cast<LaneRec *>(count_smem_raw + (size_t)(CT_NT / 32) * (STAGE + 4) *
                                                                   sizeof(int32_t))[warp];
+  if (lane == 0) {
+    stage[STAGE] = 0;  // zero guard word after the stage
+    mbar_init(&rec.mbar);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  uint32_t mbar_parity = 0;  // parity of rec.mbar's next phase
   const uint64_t t_start = P.timeout_ns ? global_ns() : 0;
   // (task, v) whose N(G_jk, v) is in `stage`, and how it is stored
   unsigned long long staged_tag = ~0ull;
-  int staged_len = 0, staged_log2h = 0, staged_mode = ST_NONE;
+  int staged_len = 0, staged_log2h = 0, staged_mode = ST_NONE, staged_off = 0;
   int32_t staged_first = 0;
+  uint32_t staged_gw = STAGE;  // bitmap: index of its zero guard word
+  bool failed = false;
 
   for (;;) {
     unsigned long long it = 0;
@@ -273,7 +366,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= (unsigned long long)P.nitems) break;
     if (P.timeout_ns && global_ns() - t_start > P.timeout_ns) {
-      if (lane == 0) atomicExch(P.status, 1);
+      if (lane == 0) atomicExch(P.status, STATUS_TIMEOUT);
       break;
     }
     const WorkItem w = P.items[it];
@@ -284,9 +377,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
     const TaskDesc &d = P.desc[t];
     // block arrays are indexed locally: in-edge x at [x - ie_off], column
     // position q at [q - ci_*_off] (the offsets are 0 when the plan is resident)
-    const int32_t *__restrict__ ie_u = d.ie_u;
-    const int32_t *__restrict__ ie_v = d.ie_v;
-    const uint32_t *__restrict__ ie_e = d.ie_e;
+    const InEdge *__restrict__ ie = d.ie;
     const int64_t ie_off = d.ie_off;
     const uint32_t *__restrict__ rp_ik = d.rp_ik;
     const uint32_t *__restrict__ rp_jk = d.rp_jk;
@@ -299,11 +390,13 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
     unsigned long long acc = 0;
 
     int64_t base = w.x0;
+    // the records (u, v, e, f) of the current window of 32 in-edges; lanes past
+    // the item hold v = -1
+    InEdge r = base + lane < w.x1 ? ie[base + lane - ie_off] : make_int4(0, -1, 0, 0);
     while (base < w.x1) {
       const int64_t batch_x0 = base;  // in-edge of lane 0; lane l's is batch_x0 + l
-      const int64_t x = base + lane;
-      const bool valid = x < w.x1;
-      const int32_t v = valid ? ie_v[x - ie_off] : -1;
+      const int32_t v = r.y;
+      const bool valid = v >= 0;
       // in-edges are sorted by destination: lanes equal to lane 0's v form a prefix
       const int32_t v0 = __shfl_sync(0xffffffffu, v, 0);
       const unsigned eq = __ballot_sync(0xffffffffu, valid && v == v0);
@@ -322,22 +415,16 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         nb = (base + 32 < w.x1 && last_head > 0) ? last_head : nvalid;
       }
       base += nb;
-      {  // the next batch's in-edge records, into L2 while this batch runs
-        const int64_t xn = base + lane;
-        if (xn < w.x1) {
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(ie_v + (xn - ie_off)));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(ie_u + (xn - ie_off)));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(ie_e + (xn - ie_off)));
-        }
-      }
+      // the next window's records into registers while this batch runs, and the
+      // one after it into L2
+      const InEdge rn = base + lane < w.x1 ? ie[base + lane - ie_off] : make_int4(0, -1, 0, 0);
+      if (base + 32 + lane < w.x1)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ie + (base + 32 + lane - ie_off)));
       const bool active = (int)lane < nb;
-
-      int32_t u = 0;
-      int64_t e = 0;
-      if (active) {
-        u = ie_u[x - ie_off];
-        e = ie_e[x - ie_off];
-      }
+      const int32_t u = r.x;
+      const int64_t e = (int64_t)(uint32_t)r.z;
+      const int64_t f = (int64_t)(uint32_t)r.w;
+      r = rn;
       // N(G_jk, v): direct row pointers of block (j, k); [b0, b1) local to ci_jk
       int64_t b0 = 0, b1 = 0;
       if (uniform) {
@@ -351,12 +438,18 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         b0 = (int64_t)rp_jk[(v - c_j) * rs_jk] - jk_off;
         b1 = (int64_t)rp_jk[(v - c_j) * rs_jk + 1] - jk_off;
       }
-      // N(G_ik, u) restricted to entries above v (for k == j, the entries of
-      // G_ij after (u, v) itself); [s0, s1) local to ci_ik
+      // N(G_ik, u) restricted to entries above v: for k == j the entries of u's
+      // run in G_ij after (u, v) itself, [e + 1, f) from the record; else u's
+      // run in G_ik from the split table. [s0, s1) local to ci_ik
       int64_t s0 = 0, s1 = 0;
       if (active && b1 > b0) {
-        s1 = (int64_t)rp_ik[(u - c_i) * rs_ik + 1] - ik_off;
-        s0 = diag ? e + 1 - ik_off : (int64_t)rp_ik[(u - c_i) * rs_ik] - ik_off;
+        if (diag) {
+          s0 = e + 1 - ik_off;
+          s1 = f - ik_off;
+        } else {
+          s0 = (int64_t)rp_ik[(u - c_i) * rs_ik] - ik_off;
+          s1 = (int64_t)rp_ik[(u - c_i) * rs_ik + 1] - ik_off;
+        }
       }
       const uint32_t len = (uint32_t)(s1 - s0);
       const uint32_t incl = warp_inclusive_scan(len);
@@ -402,67 +495,102 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
           }
           if (mode != ST_NONE) {
             __syncwarp();
+            // A list of at least BULK_STAGE_MIN entries arrives by one bulk
+            // copy (TMA) of its aligned 16-byte span: a sorted copy straight
+            // into the stage, for the tables into the free words beside them,
+            // from which the table is then built. Shorter lists, and lists
+            // with no room beside their table, are read with plain loads.
+            const int64_t e0 = b0 & ~int64_t(3), e1 = (b1 + 3) & ~int64_t(3);
+            const bool long_list = blen >= BULK_STAGE_MIN;
+            const int32_t *src = ci_jk + b0;  // where the table build reads the list
             if (mode == ST_BITMAP) {
-              const int words4 = STAGE / 4;  // the whole bitmap: bits past the span stay 0
+              // words [0, nw) hold the window, word nw is its zero guard; only
+              // these are cleared (4-word groups up to `land`)
+              const uint32_t nw = (uint32_t)((span + 31) >> 5);
+              const int64_t land = (int64_t)((nw + 4u) & ~3u);
+              const bool bulk = long_list && land + (e1 - e0) <= STAGE;
+              if (bulk) bulk_issue(stage + land, ci_jk, e0, e1, &rec.mbar, lane);
               int4 *s4 = reinterpret_cast<int4 *>(stage);
-              for (int i = lane; i < words4; i += 32) s4[i] = make_int4(0, 0, 0, 0);
-              __syncwarp();
-              for (int i = lane; i < blen; i += 32) {
-                const uint32_t d = (uint32_t)(ci_jk[b0 + i] - first);
-                atomicOr(reinterpret_cast<unsigned *>(stage) + (d >> 5), 1u << (d & 31u));
+              for (int i = lane; i < (int)(land >> 2); i += 32) s4[i] = make_int4(0, 0, 0, 0);
+              if (bulk) {
+                failed = !bulk_wait(&rec.mbar, mbar_parity);
+                src = stage + land + (b0 - e0);
               }
+              __syncwarp();
+              if (!failed)
+                for (int i = lane; i < blen; i += 32) {
+                  const uint32_t d = (uint32_t)(src[i] - first);
+                  atomicOr(reinterpret_cast<unsigned *>(stage) + (d >> 5), 1u << (d & 31u));
+                }
               staged_first = first;
               staged_len = (int)span;
-            } else if (mode == ST_FILTER) {
+              staged_gw = nw;
+            } else if (mode == ST_FILTER || mode == ST_HASH) {
               int log2h = 5;
               while ((1 << log2h) < 2 * blen) ++log2h;
               const int hsize = 1 << log2h;
-              int4 *f4 = reinterpret_cast<int4 *>(stage);
-              for (int i = lane; i < FILTER_WORDS / 4; i += 32) f4[i] = make_int4(0, 0, 0, 0);
-              int32_t *table = stage + FILTER_WORDS;
+              const int tab0 = mode == ST_FILTER ? FILTER_WORDS : 0;
+              int32_t *table = stage + tab0;
+              const int64_t land = tab0 + hsize;
+              const bool bulk = long_list && land + (e1 - e0) <= STAGE;
+              if (bulk) bulk_issue(stage + land, ci_jk, e0, e1, &rec.mbar, lane);
+              if (mode == ST_FILTER) {
+                int4 *f4 = reinterpret_cast<int4 *>(stage);
+                for (int i = lane; i < FILTER_WORDS / 4; i += 32) f4[i] = make_int4(0, 0, 0, 0);
+              }
               for (int i = lane; i < hsize; i += 32) table[i] = EMPTY;
+              if (bulk) {
+                failed = !bulk_wait(&rec.mbar, mbar_parity);
+                src = stage + land + (b0 - e0);
+              }
               __syncwarp();
               const uint32_t hmask = (uint32_t)hsize - 1u;
-              for (int i = lane; i < blen; i += 32) {
-                const int32_t key = ci_jk[b0 + i];
-                const uint32_t fb = filter_bit(key);
-                atomicOr(reinterpret_cast<unsigned *>(stage) + (fb >> 5), 1u << (fb & 31u));
-                uint32_t h = hash_slot(key, log2h) & ~3u;
-                for (int n = 0; n < hsize; ++n) {
-                  if (atomicCAS(&table[h], EMPTY, key) == EMPTY) break;
-                  h = (h + 1) & hmask;
+              if (!failed)
+                for (int i = lane; i < blen; i += 32) {
+                  const int32_t key = src[i];
+                  if (mode == ST_FILTER) {
+                    const uint32_t fb = filter_bit(key);
+                    atomicOr(reinterpret_cast<unsigned *>(stage) + (fb >> 5), 1u << (fb & 31u));
+                  }
+                  // linear probing from the first slot of the key's 4-slot
+                  // group, the order in which hash_contains reads the table
+                  uint32_t h = hash_slot(key, log2h) & ~3u;
+                  for (int n = 0; n < hsize; ++n) {
+                    if (atomicCAS(&table[h], EMPTY, key) == EMPTY) break;
+                    h = (h + 1) & hmask;
+                  }
                 }
-              }
-              staged_log2h = log2h;
-              staged_len = blen;
-            } else if (mode == ST_HASH) {
-              int log2h = 5;
-              while ((1 << log2h) < 2 * blen) ++log2h;
-              const int hsize = 1 << log2h;
-              for (int i = lane; i < hsize; i += 32) stage[i] = EMPTY;
-              __syncwarp();
-              const uint32_t hmask = (uint32_t)hsize - 1u;
-              for (int i = lane; i < blen; i += 32) {
-                const int32_t key = ci_jk[b0 + i];
-                // linear probing from the first slot of the key's 4-slot group,
-                // the order in which hash_contains reads the table
-                uint32_t h = hash_slot(key, log2h) & ~3u;
-                for (int n = 0; n < hsize; ++n) {
-                  if (atomicCAS(&stage[h], EMPTY, key) == EMPTY) break;
-                  h = (h + 1) & hmask;
-                }
-              }
               staged_log2h = log2h;
               staged_len = blen;
             } else {
-              for (int i = lane; i < blen; i += 32) stage[i] = ci_jk[b0 + i];
+              staged_off = 0;
+              if (long_list && e1 - e0 <= STAGE) {
+                bulk_issue(stage, ci_jk, e0, e1, &rec.mbar, lane);
+                failed = !bulk_wait(&rec.mbar, mbar_parity);
+                staged_off = (int)(b0 - e0);
+              } else {
+                for (int i = lane; i < blen; i += 32) stage[i] = ci_jk[b0 + i];
+              }
               staged_len = blen;
             }
             __syncwarp();
-            staged_tag = tag;
+            staged_tag = failed ? ~0ull : tag;
             staged_mode = mode;
-            staged = true;
+            staged = !failed;
           }
+        }
+      }
+      if (failed) break;
+
+      if (diag && r.y >= 0) {
+        // the start of the next window's probe run, [e + 1, f) of its record,
+        // into L2 while this batch is looked up (the rows of the sources of
+        // one destination lie anywhere in the column array)
+        const uint32_t e_next = (uint32_t)r.z + 1u, f_next = (uint32_t)r.w;
+        if (f_next > e_next) {
+          const int32_t *q = ci_ik + ((int64_t)e_next - ik_off);
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+          if (f_next - e_next > 32u) asm volatile("prefetch.global.L2 [%0];" ::"l"(q + 32));
         }
       }
 
@@ -481,10 +609,12 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         if (staged_mode == ST_BITMAP) {
           const unsigned *__restrict__ bm = reinterpret_cast<const unsigned *>(stage);
           const int32_t first = staged_first;
+          const uint32_t gw = staged_gw;
           acc += probe_quads<2>(ci_ik, rec, totalq, lane, [&](int32_t w) -> uint32_t {
             const uint32_t dlt = (uint32_t)(w - first);
-            // values outside [first, first + STAGE * 32) read the zero guard word
-            const uint32_t word = bm[min(dlt >> 5, (uint32_t)STAGE)];
+            // values outside the window [first, first + 32 * gw) read the zero
+            // guard word gw
+            const uint32_t word = bm[min(dlt >> 5, gw)];
             return (word >> (dlt & 31u)) & 1u;
           });
         } else {
@@ -527,7 +657,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
           const int64_t lo = uniform ? b0 : rec.b0[o];
           const int64_t hi = uniform ? b1 : rec.b1[o];
           const int64_t pvw = lower_bound_dev<int32_t, int64_t>(ci_jk, lo, hi, wv);
-          atomicAdd(&P.edge_sup[ie_e[batch_x0 + o - ie_off]], 1u);
+          atomicAdd(&P.edge_sup[(uint32_t)ie[batch_x0 + o - ie_off].z], 1u);
           atomicAdd(&P.edge_sup[(int64_t)qpos + ik_off], 1u);
           atomicAdd(&P.edge_sup[pvw + jk_off], 1u);
         }
@@ -559,8 +689,9 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
                        [&](int32_t w, int) { return hash_contains(stage, log2h, w); });
       } else if (staged) {
         const int slen = staged_len;
+        const int32_t *sl = stage + staged_off;
         probe_batch<3>(ci_ik, rec, total, lane, on_hit,
-                       [&](int32_t w, int) { return sorted_contains(stage, slen, w); });
+                       [&](int32_t w, int) { return sorted_contains(sl, slen, w); });
       } else {
         probe_batch<3>(ci_ik, rec, total, lane, on_hit, [&](int32_t w, int o) {
           const int64_t lo = uniform ? b0 : rec.b0[o];
@@ -580,7 +711,9 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
     if (lane == 0 && acc) atomicAdd(&P.task_count[t], acc);
     if (P.task_cycles && lane == 0)
       atomicAdd(&P.task_cycles[t], (unsigned long long)(clock64() - t_item));
+    if (failed) break;
   }
+  if (failed && lane == 0) atomicExch(P.status, STATUS_COPY_WAIT);
 }
 
 __global__ void k_sum_u64(const unsigned long long *__restrict__ in, int64_t count,
@@ -728,6 +861,16 @@ bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t n
   return BBTC_OK;
 }
 
+bbtc_status count_status_error(const char *where, int32_t status, uint32_t timeout_ms) {
+  if (status == STATUS_TIMEOUT) {
+    set_error("%s: the counting kernel passed its %u ms limit", where, timeout_ms);
+    return BBTC_ETIMEOUT;
+  }
+  set_error("%s: a bulk copy into the counting kernel's shared memory did not complete within "
+            "its wait limit (status %d)", where, (int)status);
+  return BBTC_EINTERNAL;
+}
+
 bbtc_status count_finish(const Plan &pl, cudaStream_t s) {
   k_sum_u64<<<grid_for(pl.ntasks, 256, 2), 256, 0, s>>>(pl.scratch + SCR_TASKS, pl.ntasks,
                                                          pl.scratch + SCR_TOTAL);
@@ -848,10 +991,7 @@ bbtc_status count_plans(bbtc_graph *const *gs, int32_t ng, uint32_t timeout_ms, 
   BBTC_CUDA(cudaMemcpyAsync(h.data(), counters, sizeof(unsigned long long) * h.size(),
                             cudaMemcpyDeviceToHost, s));
   BBTC_CUDA(cudaStreamSynchronize(s));
-  if ((int32_t)h[1] != 0) {
-    set_error("bbtc_count_batch: the counting kernel passed its %u ms limit", timeout_ms);
-    return BBTC_ETIMEOUT;
-  }
+  if ((int32_t)h[1] != 0) return count_status_error("bbtc_count_batch", (int32_t)h[1], timeout_ms);
   for (int32_t i = 0; i < ng; ++i) {
     uint64_t c = 0;
     const int64_t b = task_base[(size_t)i];
@@ -883,8 +1023,12 @@ static_assert(NOALLOC_TASKS + NOALLOC_MAX_P * (NOALLOC_MAX_P + 1) * (NOALLOC_MAX
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_WORDS];
 
 // Device address of g_noalloc_scratch on each device (the host-side symbol is
-// only a stand-in and must never be handed to a kernel).
+// only a stand-in and must never be handed to a kernel). Each device's entry
+// is looked up once, under a per-device once-flag, so that host threads making
+// their first call at the same time do not race on it.
 unsigned long long *g_noalloc_addr[64] = {nullptr};
+cudaError_t g_noalloc_err[64] = {cudaSuccess};
+std::once_flag g_noalloc_once[64];
 
 bbtc_status noalloc_scratch(unsigned long long **out) {
   int dev = 0;
@@ -893,10 +1037,15 @@ bbtc_status noalloc_scratch(unsigned long long **out) {
     set_error("bbtc_count_noalloc: device ordinal %d out of range", dev);
     return BBTC_EINVAL;
   }
-  if (!g_noalloc_addr[dev]) {
+  std::call_once(g_noalloc_once[dev], [dev] {
     void *ptr = nullptr;
-    BBTC_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-    g_noalloc_addr[dev] = static_cast<unsigned long long *>(ptr);
+    g_noalloc_err[dev] = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (g_noalloc_err[dev] == cudaSuccess) g_noalloc_addr[dev] = static_cast<unsigned long long *>(ptr);
+  });
+  if (g_noalloc_err[dev] != cudaSuccess) {
+    set_error("bbtc_count_noalloc: cudaGetSymbolAddress failed: %s",
+              cudaGetErrorString(g_noalloc_err[dev]));
+    return BBTC_ECUDA;
   }
   *out = g_noalloc_addr[dev];
   return BBTC_OK;

@@ -11,10 +11,16 @@ namespace bbtc {
 // more (the extra entries are never counted).
 inline int64_t padded_columns(int64_t m) { return ((m + 3) & ~int64_t(3)) + 4; }
 
+// One in-edge of block G_ab (a = part(u), b = part(v)), 16 bytes: source u,
+// destination v, the position e of (u, v) among the columns, and the end f of
+// u's run in block G_ab (one past its last column), so that for the diagonal
+// tasks (i, j, j) the probe run of (u, v) is [e + 1, f) with no lookup.
+// Positions are uint32 stored in int32 fields.
+using InEdge = int4;
+
 // Where the counting kernel finds the three blocks of task t = (i, j, k):
-//  - the in-edges of G_ij (source u, destination v, position of (u,v) among
-//    the columns), grouped by v: element x of the task's range lives at
-//    ie_*[x - ie_off];
+//  - the in-edges of G_ij, grouped by v: element x of the task's range lives
+//    at ie[x - ie_off];
 //  - N(G_ik, u) for u in V_i: columns [rp_ik[r * rs_ik], rp_ik[r * rs_ik + 1])
 //    with r = u - c_i, of ci_ik, where column position q lives at
 //    ci_ik[q - ci_ik_off];
@@ -25,9 +31,7 @@ inline int64_t padded_columns(int64_t m) { return ((m + 3) & ~int64_t(3)) + 4; }
 // per-block copies (rs = 1). For k == j, G_ik is G_ij and the in-edge
 // position indexes it directly.
 struct TaskDesc {
-  const int32_t *ie_u;
-  const int32_t *ie_v;
-  const uint32_t *ie_e;
+  const InEdge *ie;
   int64_t ie_off;
   const uint32_t *rp_ik;
   const int32_t *ci_ik;
@@ -71,9 +75,7 @@ struct Plan {
   int64_t h_rpb[64 * 64] = {0};
   int64_t total_rp = 0;
   TaskDesc *desc = nullptr;     // T, in Alg. 4 order
-  int32_t *ie_u = nullptr;      // m: in-edges grouped by (part(u), v): source u
-  int32_t *ie_v = nullptr;      // m: destination v
-  uint32_t *ie_e = nullptr;     // m: position of the edge (u,v) in the columns
+  InEdge *ie = nullptr;         // m: in-edges grouped by (part(u), v)
   int64_t *boff = nullptr;      // p*(p+1): block (i,j) in-edges = [boff[i*(p+1)+j], +1)
   int32_t *tasks = nullptr;     // 3*T: (i,j,k) in Alg. 4 order
   double *est = nullptr;        // T: ExecTime in Alg. 4 order
@@ -94,9 +96,7 @@ struct Plan {
   bool streamed = false;
   uint32_t *h_rp = nullptr;
   int32_t *h_ci = nullptr;
-  int32_t *h_ie_u = nullptr;
-  int32_t *h_ie_v = nullptr;
-  uint32_t *h_ie_e = nullptr;
+  InEdge *h_ie = nullptr;
   uint64_t bytes = 0;
 };
 
@@ -108,6 +108,9 @@ struct StreamStatsLite {
   int64_t rounds = 0;
   uint64_t h2d_bytes = 0;
   double copy_ms = 0;
+  uint64_t block_bytes = 0;
+  uint64_t device_peak = 0;
+  int32_t mode = 0;
 };
 
 struct bbtc_graph {
@@ -185,6 +188,9 @@ bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t n
                          cudaStream_t s, unsigned long long *task_cycles = nullptr,
                          unsigned *edge_sup = nullptr);
 bbtc_status count_finish(const Plan &pl, cudaStream_t s);
+// The error of a nonzero status word left by the counting kernel: 1 = it
+// passed opts.timeout_ms (ETIMEOUT), 2 = a bulk copy wait ran out (EINTERNAL).
+bbtc_status count_status_error(const char *where, int32_t status, uint32_t timeout_ms);
 
 // Counts the handles gs[0, ng) (each holding a resident plan) in one
 // persistent launch over all their work items; counts[i] is gs[i]'s total.
@@ -203,6 +209,9 @@ struct StreamStats {
   int64_t rounds = 0;
   uint64_t h2d_bytes = 0;
   double copy_ms = 0, count_ms = 0, total_ms = 0;
+  uint64_t block_bytes = 0;  // every streamed block once
+  uint64_t device_peak = 0;  // pool high-water mark during the count
+  int32_t mode = 0;          // 1: block CSRs resident, in-edge blocks once; 2: general
 };
 bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
                                unsigned long long *vertex_count, bool per_graph,

@@ -44,9 +44,13 @@ __global__ void k_cuts(const int64_t *__restrict__ rowptr, int64_t n, int p,
 // so one global counter per hub would serialise. Each CTA takes a contiguous
 // share of the part's edges and counts destinations in the top IE_HUB
 // positions in shared memory, adding to the global counters once per CTA.
+// Counters are 32-bit (positions relative to the part's first edge), and the
+// scatter, whose atomics return the slot, runs over slabs of at most IE_SLAB
+// destinations, so that a slab's counters (64 MB) stay in L2.
 constexpr int IE_NT = 256;
 constexpr int IE_NT_S = 512;  // scatter CTAs: more threads to keep position atomics in flight
 constexpr int IE_HUB = 8192;
+constexpr int64_t IE_SLAB = 16ll << 20;
 
 __device__ __forceinline__ void ie_share(int64_t e0, int64_t e1, int64_t *b0, int64_t *b1) {
   const int64_t per = (e1 - e0 + gridDim.x - 1) / gridDim.x;
@@ -58,8 +62,7 @@ __device__ __forceinline__ void ie_share(int64_t e0, int64_t e1, int64_t *b0, in
 __global__ void __launch_bounds__(IE_NT) k_inedge_count(const int64_t *__restrict__ rowptr,
                                                         const int32_t *__restrict__ colidx,
                                                         const int32_t *__restrict__ cuts, int a,
-                                                        int64_t n,
-                                                        unsigned long long *__restrict__ hist) {
+                                                        int64_t n, unsigned *__restrict__ hist) {
   __shared__ unsigned sm[IE_HUB];
   const int32_t c_a = cuts[a];
   const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
@@ -71,11 +74,24 @@ __global__ void __launch_bounds__(IE_NT) k_inedge_count(const int64_t *__restric
   for (int64_t e = b0 + threadIdx.x; e < b1; e += IE_NT) {
     const int32_t v = colidx[e];
     if (v >= hub0) atomicAdd(&sm[v - hub0], 1u);
-    else atomicAdd(&hist[v - c_a], 1ull);
+    else atomicAdd(&hist[v - c_a], 1u);
   }
   __syncthreads();
   for (int64_t i = threadIdx.x; i < n - hub0; i += IE_NT)
-    if (sm[i]) atomicAdd(&hist[hub0 - c_a + i], (unsigned long long)sm[i]);
+    if (sm[i]) atomicAdd(&hist[hub0 - c_a + i], sm[i]);
+}
+
+// 32-bit counts to 64-bit (for the scan), and the scanned offsets back to the
+// 32-bit cursors of the scatter (offsets within a part are below 2^32).
+__global__ void k_widen(const unsigned *__restrict__ in, int64_t count, uint64_t *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+__global__ void k_narrow(const uint64_t *__restrict__ in, int64_t count, unsigned *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (unsigned)in[i];
 }
 
 // Step 2 (after an exclusive scan of the counts): the block offsets of part a,
@@ -98,35 +114,41 @@ __global__ void k_inedge_offsets(const int64_t *__restrict__ rowptr,
   boff[a * (p + 1) + j] = off;
 }
 
-// Step 3: scatter each edge of part a to its destination's run, as one
-// 16-byte record (source, destination, CSR position) so that each random
-// write touches one sector; within a run the order of the sources is whatever
-// the atomics give (counts do not depend on it). For hub destinations the CTA
-// first counts its share, reserves one range per hub with a single global
-// atomic, and hands out positions inside it from shared memory.
+// Step 3: scatter each edge of part a whose destination lies in the slab
+// [v_lo, v_hi) to its destination's run, as one 16-byte record (source u,
+// destination v, CSR position e, end f of u's run in v's block, from the
+// split table row of u) so that each random write touches one sector; within
+// a run the order of the sources is whatever the atomics give (counts do not
+// depend on it). For the slab's top IE_HUB destinations the CTA first counts
+// its share, reserves one range per destination with a single global atomic,
+// and hands out positions inside it from shared memory.
 __global__ void __launch_bounds__(IE_NT_S) k_inedge_scatter(const int64_t *__restrict__ rowptr,
                                                             const int32_t *__restrict__ colidx,
                                                             const int32_t *__restrict__ esrc,
-                                                            const int32_t *__restrict__ cuts, int a,
-                                                            int64_t n,
-                                                            unsigned long long *__restrict__ offs,
-                                                            int4 *__restrict__ rec) {
+                                                            const int32_t *__restrict__ cuts_g,
+                                                            int a, int p, int64_t v_lo,
+                                                            int64_t v_hi,
+                                                            const uint32_t *__restrict__ spl_a,
+                                                            unsigned *__restrict__ offs,
+                                                            InEdge *__restrict__ rec) {
   __shared__ unsigned sm[IE_HUB];
-  const int32_t c_a = cuts[a];
-  const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
-  const int64_t hub0 = n - IE_HUB > c_a ? n - IE_HUB : c_a;
+  __shared__ int32_t cuts[MAXP + 1];
+  for (int i = threadIdx.x; i <= p; i += IE_NT_S) cuts[i] = cuts_g[i];
+  const int32_t c_a = cuts_g[a];
+  const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts_g[a + 1]];
+  const int64_t hub0 = v_hi - IE_HUB > v_lo ? v_hi - IE_HUB : v_lo;
   for (int i = threadIdx.x; i < IE_HUB; i += IE_NT_S) sm[i] = 0;
   __syncthreads();
   int64_t b0, b1;
   ie_share(e0, e1, &b0, &b1);
   for (int64_t e = b0 + threadIdx.x; e < b1; e += IE_NT_S) {
     const int32_t v = colidx[e];
-    if (v >= hub0) atomicAdd(&sm[v - hub0], 1u);
+    if (v >= hub0 && v < v_hi) atomicAdd(&sm[v - hub0], 1u);
   }
   __syncthreads();
   // positions are relative to e0 and below 2^32
-  for (int64_t i = threadIdx.x; i < n - hub0; i += IE_NT_S)
-    if (sm[i]) sm[i] = (unsigned)atomicAdd(&offs[hub0 - c_a + i], (unsigned long long)sm[i]);
+  for (int64_t i = threadIdx.x; i < v_hi - hub0; i += IE_NT_S)
+    if (sm[i]) sm[i] = atomicAdd(&offs[hub0 - c_a + i], sm[i]);
   __syncthreads();
   // IE_ILP edges per thread per step: their position atomics are in flight together
   constexpr int IE_ILP = 4;
@@ -137,31 +159,23 @@ __global__ void __launch_bounds__(IE_NT_S) k_inedge_scatter(const int64_t *__res
     for (int r = 0; r < IE_ILP; ++r) {
       const int64_t idx = e + (int64_t)r * IE_NT_S;
       v[r] = idx < b1 ? colidx[idx] : -1;
+      if (v[r] < v_lo || v[r] >= v_hi) v[r] = -1;  // outside the slab (or past the share)
     }
 #pragma unroll
     for (int r = 0; r < IE_ILP; ++r)
       if (v[r] >= 0)
         x[r] = v[r] >= hub0 ? (uint64_t)atomicAdd(&sm[v[r] - hub0], 1u)
-                            : (uint64_t)atomicAdd(&offs[v[r] - c_a], 1ull);
+                            : (uint64_t)atomicAdd(&offs[v[r] - c_a], 1u);
 #pragma unroll
     for (int r = 0; r < IE_ILP; ++r) {
       const int64_t idx = e + (int64_t)r * IE_NT_S;
-      if (v[r] >= 0)
-        rec[e0 + (int64_t)x[r]] = make_int4(esrc[idx], v[r], (int32_t)(uint32_t)idx, 0);
+      if (v[r] >= 0) {
+        const int32_t u = esrc[idx];
+        const int b = part_of_dev(cuts, p, v[r]);  // >= a: v > u
+        const uint32_t f = spl_a[(int64_t)(u - c_a) * (p - a + 1) + (b - a + 1)];
+        rec[e0 + (int64_t)x[r]] = make_int4(u, v[r], (int32_t)(uint32_t)idx, (int32_t)f);
+      }
     }
-  }
-}
-
-// Step 4 (all parts): the records, now in in-edge order, to the three arrays.
-__global__ void k_inedge_unpack(const int4 *__restrict__ rec, int64_t m,
-                                int32_t *__restrict__ ie_u, int32_t *__restrict__ ie_v,
-                                uint32_t *__restrict__ ie_e) {
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int4 r = rec[x];
-    ie_u[x] = r.x;
-    ie_v[x] = r.y;
-    ie_e[x] = (uint32_t)r.z;
   }
 }
 
@@ -193,12 +207,18 @@ __global__ void k_splits(const int64_t *__restrict__ rowptr, const int32_t *__re
   }
 }
 
-// In-edge positions from CSR positions to physical block positions.
-__global__ void k_remap_positions(uint32_t *__restrict__ ie_e, int64_t m,
+// In-edge positions from CSR positions to physical block positions: e maps
+// through pos_of_edge, and the run end f to one past the mapped position of
+// the run's last edge (f - 1 >= e lies in the same run).
+__global__ void k_remap_positions(InEdge *__restrict__ ie, int64_t m,
                                   const uint32_t *__restrict__ pos_of_edge) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < m;
-       x += (int64_t)gridDim.x * blockDim.x)
-    ie_e[x] = pos_of_edge[ie_e[x]];
+       x += (int64_t)gridDim.x * blockDim.x) {
+    InEdge r = ie[x];
+    r.z = (int32_t)pos_of_edge[(uint32_t)r.z];
+    r.w = (int32_t)(pos_of_edge[(uint32_t)r.w - 1u] + 1u);
+    ie[x] = r;
+  }
 }
 
 // BCSR, step 1 (one thread per oriented edge e = (u, v)): the edge falls in
@@ -325,33 +345,36 @@ __global__ void k_item_counts(const int32_t *__restrict__ order,
   }
 }
 
+// One thread per work item q: the task at position x of the order with
+// first[x] <= q < first[x + 1] (binary search), and its chunk q - first[x].
 __global__ void k_item_fill(const int32_t *__restrict__ order, const int32_t *__restrict__ tasks,
-                            const int64_t *__restrict__ boff, const int32_t *__restrict__ cuts,
-                            int p, int64_t nt, int64_t chunk, const uint64_t *__restrict__ first,
+                            const int64_t *__restrict__ boff, int p, int64_t nt, int64_t chunk,
+                            const uint64_t *__restrict__ first, uint64_t nitems,
                             int kernel_mode, int32_t hash_threshold,
                             WorkItem *__restrict__ items) {
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nt;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t n_items = first[x + 1] - first[x];
-    if (n_items == 0) continue;
-    const int t = order[x];
-    const int i = tasks[3 * t], j = tasks[3 * t + 1], k = tasks[3 * t + 2];
-    const int64_t b0 = boff[i * (p + 1) + j], b1 = boff[i * (p + 1) + j + 1];
-    // isDense (Alg. 7), decided per staged list N(G_jk, v) by the counting
-    // kernel: bits 0-1 = 0 INTERSECT (sorted search), 1 HASHMAP, 2 AUTO;
-    // bits 2.. = the AUTO length above which a list that does not fit a
-    // bitmap is hashed rather than searched
-    const int32_t flags = kernel_mode == BBTC_KERNEL_HASHMAP     ? 1
-                          : kernel_mode == BBTC_KERNEL_INTERSECT ? 0
-                                                                 : 2 | (hash_threshold << 2);
-    for (uint64_t c = 0; c < n_items; ++c) {
-      WorkItem w;
-      w.task = t;
-      w.flags = flags;
-      w.x0 = b0 + (int64_t)c * chunk;
-      w.x1 = w.x0 + chunk < b1 ? w.x0 + chunk : b1;
-      items[first[x] + c] = w;
+  // isDense (Alg. 7), decided per staged list N(G_jk, v) by the counting
+  // kernel: bits 0-1 = 0 INTERSECT (sorted search), 1 HASHMAP, 2 AUTO;
+  // bits 2.. = the AUTO length above which a list that does not fit a
+  // bitmap is hashed rather than searched
+  const int32_t flags = kernel_mode == BBTC_KERNEL_HASHMAP     ? 1
+                        : kernel_mode == BBTC_KERNEL_INTERSECT ? 0
+                                                               : 2 | (hash_threshold << 2);
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nitems;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = nt;  // last x with first[x] <= q
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (first[mid] <= q) lo = mid; else hi = mid;
     }
+    const int t = order[lo];
+    const int i = tasks[3 * t], j = tasks[3 * t + 1];
+    const int64_t b0 = boff[i * (p + 1) + j], b1 = boff[i * (p + 1) + j + 1];
+    WorkItem w;
+    w.task = t;
+    w.flags = flags;
+    w.x0 = b0 + (int64_t)(q - first[lo]) * chunk;
+    w.x1 = w.x0 + chunk < b1 ? w.x0 + chunk : b1;
+    items[q] = w;
   }
 }
 
@@ -359,9 +382,7 @@ __global__ void k_item_fill(const int32_t *__restrict__ order, const int32_t *__
 
 void free_plan(Plan *pl, cudaStream_t s) {
   dfree(pl->cuts, s);
-  dfree(pl->ie_u, s);
-  dfree(pl->ie_v, s);
-  dfree(pl->ie_e, s);
+  dfree(pl->ie, s);
   dfree(pl->boff, s);
   dfree(pl->tasks, s);
   dfree(pl->est, s);
@@ -402,7 +423,6 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   pl.partition = partition;
   pl.ntasks = (int64_t)p * (p + 1) * (p + 2) / 6;
   const int64_t n = g->n, m = g->m;
-  const int nb = g->nb;
   Scratch scratch(s);
   bbtc_status st = BBTC_OK;
 #define PLAN_TRY(expr)          \
@@ -457,19 +477,16 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
 
   // in-edges grouped by (part(u), v), and the block offsets: one counting
   // sort on the destination per part
-  PLAN_TRY(dalloc_n(&pl.ie_u, m, s));
-  PLAN_TRY(dalloc_n(&pl.ie_v, m, s));
-  PLAN_TRY(dalloc_n(&pl.ie_e, m, s));
+  PLAN_TRY(dalloc_n(&pl.ie, m, s));
   PLAN_TRY(dalloc_n(&pl.boff, (int64_t)p * (p + 1), s));
   {
-    unsigned long long *hist = nullptr;
-    int4 *rec = nullptr;
+    unsigned *hist = nullptr;  // counts, then the scatter's cursors
+    uint64_t *scan = nullptr;
     PLAN_TRY(scratch.get(&hist, n + 1));
-    PLAN_TRY(scratch.get(&rec, m > 0 ? m : 1));
+    PLAN_TRY(scratch.get(&scan, n + 1));
     for (int a = 0; a < p; ++a) {
       const int64_t bins = n - pl.h_cuts[a];
-      if (cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (size_t)(bins + 1), s) !=
-          cudaSuccess) {
+      if (cudaMemsetAsync(hist, 0, sizeof(unsigned) * (size_t)(bins + 1), s) != cudaSuccess) {
         set_error("build_plan: cudaMemsetAsync failed");
         free_plan(&pl, s);
         return BBTC_ECUDA;
@@ -480,20 +497,25 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
         k_inedge_count<<<ie_grid, IE_NT, 0, s>>>(g->rowptr, g->colidx, pl.cuts, a, n, hist);
         PLAN_TRY(launch_status("build_plan"));
       }
-      if (bins > 0)
-        PLAN_TRY(exclusive_scan_u64(reinterpret_cast<uint64_t *>(hist),
-                                    reinterpret_cast<uint64_t *>(hist), bins, s));
-      k_inedge_offsets<<<1, MAXP + 1, 0, s>>>(g->rowptr, pl.cuts, a, p, hist, bins, pl.boff);
-      PLAN_TRY(launch_status("build_plan"));
-      if (m > 0) {
-        k_inedge_scatter<<<ie_grid, IE_NT_S, 0, s>>>(g->rowptr, g->colidx, g->esrc, pl.cuts, a,
-                                                      n, hist, rec);
+      if (bins > 0) {
+        k_widen<<<grid_for(bins, 256, 16), 256, 0, s>>>(hist, bins, scan);
+        PLAN_TRY(launch_status("build_plan"));
+        PLAN_TRY(exclusive_scan_u64(scan, scan, bins, s));
+        k_narrow<<<grid_for(bins, 256, 16), 256, 0, s>>>(scan, bins, hist);
         PLAN_TRY(launch_status("build_plan"));
       }
-    }
-    if (m > 0) {
-      k_inedge_unpack<<<grid_for(m, 256, 32), 256, 0, s>>>(rec, m, pl.ie_u, pl.ie_v, pl.ie_e);
+      k_inedge_offsets<<<1, MAXP + 1, 0, s>>>(g->rowptr, pl.cuts, a, p,
+                                               reinterpret_cast<const unsigned long long *>(scan),
+                                               bins, pl.boff);
       PLAN_TRY(launch_status("build_plan"));
+      if (m > 0)
+        for (int64_t v_lo = pl.h_cuts[a]; v_lo < n; v_lo += IE_SLAB) {
+          const int64_t v_hi = v_lo + IE_SLAB < n ? v_lo + IE_SLAB : n;
+          k_inedge_scatter<<<ie_grid, IE_NT_S, 0, s>>>(g->rowptr, g->colidx, g->esrc, pl.cuts, a,
+                                                        p, v_lo, v_hi, pl.spl + pl.h_spl_off[a],
+                                                        hist, pl.ie);
+          PLAN_TRY(launch_status("build_plan"));
+        }
     }
   }
 
@@ -529,9 +551,7 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
       for (int j = i; j < p; ++j)
         for (int k = j; k < p; ++k, ++t) {
           TaskDesc &d = h_desc[t];
-          d.ie_u = pl.ie_u;
-          d.ie_v = pl.ie_v;
-          d.ie_e = pl.ie_e;
+          d.ie = pl.ie;
           d.ie_off = 0;
           d.rp_ik = pl.spl + pl.h_spl_off[i] + (k - i);
           d.rs_ik = p - i + 1;
@@ -582,16 +602,16 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
   pl.nitems = (int64_t)nitems;
   PLAN_TRY(dalloc_n(&pl.items, pl.nitems, s));
   if (nitems > 0) {
-    k_item_fill<<<grid_for(nt, 256, 4), 256, 0, s>>>(pl.order, pl.tasks, pl.boff, pl.cuts, p, nt,
-                                                     chunk, first, kernel_mode, hash_threshold,
-                                                     pl.items);
+    k_item_fill<<<grid_for((int64_t)nitems, 256, 8), 256, 0, s>>>(
+        pl.order, pl.tasks, pl.boff, p, nt, chunk, first, nitems, kernel_mode, hash_threshold,
+        pl.items);
     PLAN_TRY(launch_status("build_plan"));
   }
   // counting scratch and kernel configuration, so that a count only enqueues
   PLAN_TRY(dalloc_n(&pl.scratch, SCR_TASKS + nt + g->ng, s));
   PLAN_TRY(configure_count_kernels(&pl));
 #undef PLAN_TRY
-  pl.bytes = (uint64_t)m * 12 + (uint64_t)pl.h_spl_off[p] * 4 + (uint64_t)nt * (24 + sizeof(TaskDesc)) +
+  pl.bytes = (uint64_t)m * sizeof(InEdge) + (uint64_t)pl.h_spl_off[p] * 4 + (uint64_t)nt * (24 + sizeof(TaskDesc)) +
              (uint64_t)pl.nitems * sizeof(WorkItem) + (uint64_t)(SCR_TASKS + nt + g->ng) * 8;
   g->plan = pl;
   return BBTC_OK;
@@ -634,7 +654,7 @@ bbtc_status plan_physical_blocks(const bbtc_graph *g, Plan &pl, cudaStream_t s) 
     k_bcsr_fill<<<grid_for(m, 256, 32), 256, 0, s>>>(g->esrc, g->colidx, m, pl.cuts, p, d_rpb,
                                                      cnt, start, pl.ci, pos_of_edge);
     BBTC_LAUNCH_CHECK();
-    k_remap_positions<<<grid_for(m, 256, 32), 256, 0, s>>>(pl.ie_e, m, pos_of_edge);
+    k_remap_positions<<<grid_for(m, 256, 32), 256, 0, s>>>(pl.ie, m, pos_of_edge);
     BBTC_LAUNCH_CHECK();
   }
   k_bcsr_rowptr<<<grid_for(pl.total_rp, 256, 32), 256, 0, s>>>(cnt, pl.total_rp, pl.rp);

@@ -291,6 +291,9 @@ __global__ void k_tile_rows(const int64_t *__restrict__ rowptr, int64_t n, int64
 // degree of u += first copies of v != u, flag unsorted rows and out-of-range
 // ids. MODE 1: out-degree at rank(u) += first copies with rank(v) > rank(u).
 // MODE 2: scatter rank(v) into row rank(u) (any order; rows are sorted after).
+// When rr is given, MODE 1 also stores each entry's rank(v) when the entry is
+// such an upward first copy (else -1), and MODE 2 reads it back in order
+// instead of gathering rank(v) a second time.
 // For a batch (voff != nullptr), the entries of a row of graph g are local ids
 // in [0, voff[g+1] - voff[g]), shifted here by voff[g].
 template <int MODE>
@@ -306,7 +309,8 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
                                                     int32_t *__restrict__ colidx_o,
                                                     int32_t *__restrict__ esrc_o,
                                                     int32_t *__restrict__ err,
-                                                    const int64_t *__restrict__ voff, int ng) {
+                                                    const int64_t *__restrict__ voff, int ng,
+                                                    int32_t *__restrict__ rr) {
   const unsigned lane = threadIdx.x & 31u;
   const int64_t ntiles = (nnz + SP_TILE - 1) / SP_TILE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -346,6 +350,14 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
           row_end = rowptr[u + 1];
           if (MODE > 0) ru = rank[u];
         }
+        if (MODE == 2 && rr) {  // the upward rank stored by MODE 1
+          const int32_t rv = rr[e];
+          if (rv >= 0) {
+            key[i] = ru;
+            val[i] = rv;
+          }
+          continue;
+        }
         if (voff) {
           while (u >= gend && gi + 1 < ng) {
             ++gi;
@@ -365,10 +377,11 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
         const bool head = in_range && v != u && (first_in_row || prev != vl);
         if (MODE == 0) {
           key[i] = head ? u : -1;
-        } else if (head) {
-          const int32_t rv = rank[v];
-          if (rv > ru) key[i] = ru;
+        } else {
+          const int32_t rv = head ? rank[v] : -1;
+          if (head && rv > ru) key[i] = ru;
           val[i] = rv;
+          if (MODE == 1 && rr) rr[e] = head && rv > ru ? rv : -1;
         }
       }
     }
@@ -633,7 +646,7 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   const unsigned grid = grid_for(ntiles, 1, 32);
   k_sym_pass<0><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, g->deg, nullptr,
                                        nullptr, nullptr, nullptr, nullptr, nullptr, err, g->voff,
-                                       g->ng);
+                                       g->ng, nullptr);
   BBTC_LAUNCH_CHECK();
   int32_t herr = 0;
   BBTC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -681,9 +694,21 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   BBTC_TRY(dalloc_n(&g->rowptr, n + 1, s));
   g->bytes += (uint64_t)(n + 1) * 8;
   BBTC_CUDA(cudaMemsetAsync(g->rowptr, 0, sizeof(int64_t) * (size_t)(n + 1), s));
+  // each entry's upward rank, kept for the scatter pass (it is skipped, and the
+  // scatter gathers the ranks again, when the nnz-entry array does not fit)
+  int32_t *rr = nullptr;
+  if (dalloc_n(&rr, nnz, s) != BBTC_OK) {
+    clear_error();
+    rr = nullptr;
+  }
+  struct FreeRR {
+    int32_t *p;
+    cudaStream_t s;
+    ~FreeRR() { dfree(p, s); }
+  } free_rr{rr, s};
   k_sym_pass<1><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, nullptr, rank,
                                        reinterpret_cast<unsigned long long *>(g->rowptr),
-                                       nullptr, nullptr, nullptr, nullptr, err, g->voff, g->ng);
+                                       nullptr, nullptr, nullptr, nullptr, err, g->voff, g->ng, rr);
   BBTC_LAUNCH_CHECK();
   int64_t *stats = nullptr;
   BBTC_TRY(scratch.get(&stats, 2));
@@ -709,7 +734,7 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   BBTC_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned int) * (size_t)(n > 0 ? n : 1), s));
   k_sym_pass<2><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, nullptr, rank,
                                        nullptr, g->rowptr, cursor, g->colidx, g->esrc, err,
-                                       g->voff, g->ng);
+                                       g->voff, g->ng, rr);
   BBTC_LAUNCH_CHECK();
   if (m > 0) {
     if (g->dplus_max <= SEG_CAP) {

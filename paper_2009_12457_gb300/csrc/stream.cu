@@ -1,14 +1,24 @@
 // stream.cu -- a11: counting with the blocks streamed from pinned host memory.
 //
 // When a caller gives bbtc_count a device budget, the plan's block arrays
-// (each block G_ab's row pointers and columns, and each block's in-edges) move
-// to pinned host memory. Tasks are then processed in the plan's order, in
-// rounds. The device pool of `budget` bytes holds blocks at fixed offsets:
-// a round is the longest run of consecutive tasks whose blocks are either
-// already in the pool or fit beside the blocks of the round still being
-// counted. While one round is counted on the compute stream, the next round's
-// missing blocks are copied on a copy stream (the paper's prefetch of the next
-// task's blocks, Alg. 7); blocks that stay in the pool are not copied again.
+// (each block G_ab's row pointers and columns, and each block's in-edge
+// records) move to pinned host memory, and the plan's work items are put in
+// Alg. 4's task order, so that the tasks (i, j, k), k >= j, which share the
+// in-edge block of G_ij, are consecutive. The counting step then holds at
+// most `budget` bytes of blocks on the device, in one pool, in one of two
+// ways:
+//  1. When every block CSR fits in the pool beside two in-edge buffers, the
+//     block CSRs are copied once and stay, and the in-edge blocks are copied
+//     once each, group by group (one group = the tasks of one G_ij): the next
+//     group's in-edges are copied on a copy stream into the other buffer
+//     while the current group counts (the paper's prefetch of the next task's
+//     blocks, Alg. 7). Every block crosses to the device exactly once.
+//  2. Otherwise, tasks are taken in that order in rounds: a round is the
+//     longest run of consecutive tasks whose blocks are either already in the
+//     pool or fit beside the blocks of the round still being counted. Blocks
+//     sit at fixed offsets; one still in the pool when a later round needs it
+//     is used in place, and one that was overwritten is copied again. Round
+//     r+1's copies overlap round r's count.
 // Each task's descriptor is rewritten to point at its blocks in the pool.
 // Counts accumulate across rounds exactly as in one launch.
 #include <stdio.h>
@@ -101,25 +111,33 @@ bbtc_status plan_to_host(const bbtc_graph *g, Plan &pl, int64_t m, cudaStream_t 
   BBTC_TRY(plan_physical_blocks(g, pl, s));
   BBTC_TRY(to_pinned(&pl.h_rp, &pl.rp, pl.total_rp, s));
   BBTC_TRY(to_pinned(&pl.h_ci, &pl.ci, m, s));
-  BBTC_TRY(to_pinned(&pl.h_ie_u, &pl.ie_u, m, s));
-  BBTC_TRY(to_pinned(&pl.h_ie_v, &pl.ie_v, m, s));
-  BBTC_TRY(to_pinned(&pl.h_ie_e, &pl.ie_e, m, s));
+  BBTC_TRY(to_pinned(&pl.h_ie, &pl.ie, m, s));
   BBTC_CUDA(cudaStreamSynchronize(s));
   dfree(pl.rp, s);
   dfree(pl.ci, s);
-  dfree(pl.ie_u, s);
-  dfree(pl.ie_v, s);
-  dfree(pl.ie_e, s);
+  dfree(pl.ie, s);
   pl.rp = nullptr;
   pl.ci = nullptr;
-  pl.ie_u = pl.ie_v = nullptr;
-  pl.ie_e = nullptr;
+  pl.ie = nullptr;
+  // work items in Alg. 4 task order (a task's items stay together and keep
+  // their order), so that the tasks sharing an in-edge block are consecutive
+  if (pl.nitems > 0) {
+    std::vector<WorkItem> items((size_t)pl.nitems);
+    BBTC_CUDA(cudaMemcpyAsync(items.data(), pl.items, sizeof(WorkItem) * items.size(),
+                              cudaMemcpyDeviceToHost, s));
+    BBTC_CUDA(cudaStreamSynchronize(s));
+    std::stable_sort(items.begin(), items.end(),
+                     [](const WorkItem &a, const WorkItem &b) { return a.task < b.task; });
+    BBTC_CUDA(cudaMemcpyAsync(pl.items, items.data(), sizeof(WorkItem) * items.size(),
+                              cudaMemcpyHostToDevice, s));
+    BBTC_CUDA(cudaStreamSynchronize(s));
+  }
   pl.streamed = true;
   return BBTC_OK;
 }
 
 // A block in the pool: kind 0 = BCSR block (a, b) (row pointers, then
-// columns), kind 1 = in-edges of block (a, b) (u, v, position).
+// columns), kind 1 = in-edge records of block (a, b).
 struct BlockKey {
   int kind, a, b;
   bool operator<(const BlockKey &o) const {
@@ -137,13 +155,10 @@ struct Run {  // the work items of one task, in plan order
 void free_plan_host(Plan *pl) {
   pinned_release(pl->h_rp);
   pinned_release(pl->h_ci);
-  pinned_release(pl->h_ie_u);
-  pinned_release(pl->h_ie_v);
-  pinned_release(pl->h_ie_e);
+  pinned_release(pl->h_ie);
   pl->h_rp = nullptr;
   pl->h_ci = nullptr;
-  pl->h_ie_u = pl->h_ie_v = nullptr;
-  pl->h_ie_e = nullptr;
+  pl->h_ie = nullptr;
 }
 
 bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
@@ -191,8 +206,20 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
   auto block_bytes = [&](const BlockKey &k) -> size_t {
     if (k.kind == 0)
       return align_up(4 * (size_t)(vsize(k.a) + 1)) + align_up(4 * (size_t)(col1(k.a, k.b) - col0(k.a, k.b)));
-    return 3 * align_up(4 * (size_t)(ie1(k.a, k.b) - ie0(k.a, k.b)));
+    return align_up(sizeof(InEdge) * (size_t)(ie1(k.a, k.b) - ie0(k.a, k.b)));
   };
+
+  // totals: every block once (exact bytes, as counted in h2d_bytes)
+  uint64_t csr_exact = 0, ie_exact = 0;
+  size_t csr_total = 0, ie_max = 0;
+  for (int a = 0; a < p; ++a)
+    for (int b = a; b < p; ++b) {
+      csr_exact += 4 * (uint64_t)(vsize(a) + 1 + col1(a, b) - col0(a, b));
+      ie_exact += sizeof(InEdge) * (uint64_t)(ie1(a, b) - ie0(a, b));
+      csr_total += block_bytes(BlockKey{0, a, b});
+      ie_max = std::max(ie_max, block_bytes(BlockKey{1, a, b}));
+    }
+  stats->block_bytes = csr_exact + ie_exact;
 
   // The pool holds blocks at fixed offsets. A round's blocks that are already
   // in the pool (copied for an earlier round and not overwritten since) are
@@ -208,6 +235,18 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
     size_t off, size;
     int64_t round;  // last round that uses the block
   };
+  const bool csr_resident = csr_total + 2 * ie_max <= pool_bytes;
+  stats->mode = csr_resident ? 1 : 2;
+  cudaMemPool_t mem_pool = nullptr;
+  {
+    int dev = 0;
+    uint64_t zero = 0;  // resets the high-water mark to the memory in use now
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetDefaultMemPool(&mem_pool, dev) == cudaSuccess)
+      cudaMemPoolSetAttribute(mem_pool, cudaMemPoolAttrUsedMemHigh, &zero);
+    else
+      mem_pool = nullptr;
+  }
   std::map<BlockKey, Slot> placed;
   cudaStream_t cs = nullptr;
   cudaEvent_t copy_done[2] = {nullptr, nullptr}, kern_done[2] = {nullptr, nullptr};
@@ -234,7 +273,118 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
     }
     if ((st = count_reset(g, pl, vertex_count, per_graph, s)) != BBTC_OK) break;
     if (cudaEventRecord(t_begin, s) != cudaSuccess) { st = BBTC_ECUDA; break; }
-    size_t pos = 0;
+    if (csr_resident) {
+      // mode 1: every block CSR once, then the in-edge blocks group by group
+      // into two alternating buffers after them
+      std::map<std::pair<int, int>, size_t> csr_off;
+      size_t off = 0;
+      // event pairs around each batch of copies (not around the waits), summed at the end
+      std::vector<std::pair<cudaEvent_t, cudaEvent_t>> copy_ev;
+      auto copy_begin = [&]() {
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, cs);
+        copy_ev.emplace_back(a, b);
+      };
+      auto copy_end = [&]() { cudaEventRecord(copy_ev.back().second, cs); };
+      copy_begin();
+      for (int a = 0; a < p && st == BBTC_OK; ++a)
+        for (int b = a; b < p; ++b) {
+          csr_off[{a, b}] = off;
+          const int64_t nrp = vsize(a) + 1, c0i = col0(a, b), nci = col1(a, b) - c0i;
+          if (cudaMemcpyAsync(pool + off, pl.h_rp + pl.h_rpb[a * p + b], 4 * (size_t)nrp,
+                              cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+              (nci > 0 && cudaMemcpyAsync(pool + off + align_up(4 * (size_t)nrp), pl.h_ci + c0i,
+                                          4 * (size_t)nci, cudaMemcpyHostToDevice,
+                                          cs) != cudaSuccess)) {
+            set_error("streamed count: host-to-device block copy failed");
+            st = BBTC_ECUDA;
+            break;
+          }
+          stats->h2d_bytes += 4 * (uint64_t)(nrp + nci);
+          off += block_bytes(BlockKey{0, a, b});
+        }
+      copy_end();
+      const size_t slot[2] = {csr_total, csr_total + ie_max};
+      size_t gpos = 0;
+      while (gpos < runs.size() && st == BBTC_OK) {
+        // one group: the consecutive tasks that share (i, j), hence G_ij's in-edges
+        const int t0 = runs[gpos].task;
+        const int i = ti[t0], j = tj[t0];
+        size_t gend = gpos;
+        while (gend < runs.size() && ti[runs[gend].task] == i && tj[runs[gend].task] == j) ++gend;
+        const int h = (int)(round & 1);
+        if (used_parity[h]) {  // the kernel of round - 2 read this buffer and stage[h]
+          if (cudaStreamWaitEvent(cs, kern_done[h], 0) != cudaSuccess ||
+              cudaEventSynchronize(copy_done[h]) != cudaSuccess) {
+            st = BBTC_ECUDA;
+            break;
+          }
+        }
+        const int64_t x0 = ie0(i, j), len = ie1(i, j) - x0;
+        copy_begin();
+        if (len > 0 && cudaMemcpyAsync(pool + slot[h], pl.h_ie + x0, sizeof(InEdge) * (size_t)len,
+                                       cudaMemcpyHostToDevice, cs) != cudaSuccess) {
+          set_error("streamed count: host-to-device block copy failed");
+          st = BBTC_ECUDA;
+          break;
+        }
+        stats->h2d_bytes += sizeof(InEdge) * (uint64_t)len;
+        for (size_t r = gpos; r < gend && st == BBTC_OK; ++r) {
+          const int t = runs[r].task;
+          const int k = tk[t];
+          const size_t o_ik = csr_off[{i, k}], o_jk = csr_off[{j, k}];
+          TaskDesc &d = stage[h][t];
+          d.ie = reinterpret_cast<const InEdge *>(pool + slot[h]);
+          d.ie_off = x0;
+          d.rp_ik = reinterpret_cast<const uint32_t *>(pool + o_ik);
+          d.rs_ik = 1;
+          d.rs_jk = 1;
+          d.ci_ik = reinterpret_cast<const int32_t *>(pool + o_ik +
+                                                      align_up(4 * (size_t)(vsize(i) + 1)));
+          d.ci_ik_off = col0(i, k);
+          d.rp_jk = reinterpret_cast<const uint32_t *>(pool + o_jk);
+          d.ci_jk = reinterpret_cast<const int32_t *>(pool + o_jk +
+                                                      align_up(4 * (size_t)(vsize(j) + 1)));
+          d.ci_jk_off = col0(j, k);
+          d.c_i = pl.h_cuts[i];
+          d.c_j = pl.h_cuts[j];
+          d.diag = k == j;
+          d.task = t;
+          if (cudaMemcpyAsync(pl.desc + t, &stage[h][t], sizeof(TaskDesc), cudaMemcpyHostToDevice,
+                              cs) != cudaSuccess) {
+            set_error("streamed count: descriptor copy failed");
+            st = BBTC_ECUDA;
+          }
+        }
+        copy_end();
+        if (st != BBTC_OK) break;
+        if (cudaEventRecord(copy_done[h], cs) != cudaSuccess ||
+            cudaStreamWaitEvent(s, copy_done[h], 0) != cudaSuccess) {
+          st = BBTC_ECUDA;
+          break;
+        }
+        st = count_launch(g, pl, runs[gpos].item0, runs[gend - 1].item1 - runs[gpos].item0,
+                          vertex_count, per_graph, timeout_ms, s, task_cycles);
+        if (st != BBTC_OK) break;
+        if (cudaEventRecord(kern_done[h], s) != cudaSuccess) {
+          st = BBTC_ECUDA;
+          break;
+        }
+        used_parity[h] = true;
+        ++round;
+        gpos = gend;
+      }
+      cudaStreamSynchronize(cs);
+      for (auto &ev : copy_ev) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) copy_ms_total += ms;
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+      }
+    }
+    size_t pos = csr_resident ? runs.size() : 0;
     while (pos < runs.size() && st == BBTC_OK) {
       // place blocks for the longest run of tasks that fits next to the
       // blocks of the round in flight (round - 1)
@@ -339,14 +489,10 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
           stats->h2d_bytes += 4 * (uint64_t)(nrp + nci);
         } else {
           const int64_t x0 = ie0(k.a, k.b), len = ie1(k.a, k.b) - x0;
-          const size_t seg = align_up(4 * (size_t)len);
-          if (len > 0) {
-            e1 = cudaMemcpyAsync(dst, pl.h_ie_u + x0, 4 * (size_t)len, cudaMemcpyHostToDevice, cs);
-            e2 = cudaMemcpyAsync(dst + seg, pl.h_ie_v + x0, 4 * (size_t)len, cudaMemcpyHostToDevice, cs);
-            e3 = cudaMemcpyAsync(dst + 2 * seg, pl.h_ie_e + x0, 4 * (size_t)len,
+          if (len > 0)
+            e1 = cudaMemcpyAsync(dst, pl.h_ie + x0, sizeof(InEdge) * (size_t)len,
                                  cudaMemcpyHostToDevice, cs);
-          }
-          stats->h2d_bytes += 12 * (uint64_t)len;
+          stats->h2d_bytes += sizeof(InEdge) * (uint64_t)len;
         }
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
           set_error("streamed count: host-to-device block copy failed");
@@ -362,11 +508,8 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
         const size_t o_ie = placed[BlockKey{1, i, j}].off;
         const size_t o_ik = placed[BlockKey{0, i, k}].off;
         const size_t o_jk = placed[BlockKey{0, j, k}].off;
-        const size_t seg = align_up(4 * (size_t)(ie1(i, j) - ie0(i, j)));
         TaskDesc &d = stage[h][t];
-        d.ie_u = reinterpret_cast<const int32_t *>(pool + o_ie);
-        d.ie_v = reinterpret_cast<const int32_t *>(pool + o_ie + seg);
-        d.ie_e = reinterpret_cast<const uint32_t *>(pool + o_ie + 2 * seg);
+        d.ie = reinterpret_cast<const InEdge *>(pool + o_ie);
         d.ie_off = ie0(i, j);
         d.rp_ik = reinterpret_cast<const uint32_t *>(pool + o_ik);
         d.rs_ik = 1;
@@ -426,6 +569,11 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
   }
   stats->rounds = round;
   stats->copy_ms = copy_ms_total;
+  if (mem_pool) {
+    uint64_t peak = 0;
+    if (cudaMemPoolGetAttribute(mem_pool, cudaMemPoolAttrUsedMemHigh, &peak) == cudaSuccess)
+      stats->device_peak = peak;
+  }
   for (cudaEvent_t e : {copy_done[0], copy_done[1], kern_done[0], kern_done[1], t_begin, t_end})
     if (e) cudaEventDestroy(e);
   for (TaskDesc *d : stage) pinned_release(d);
