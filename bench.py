@@ -11,9 +11,15 @@ the step through the same public calls from pinned HOST buffers, so the
 host-to-device copy of the input CSR and the device-to-host read of the count
 are inside the timed region.
 
+The default workload is the Friendster-shaped Chung-Lu graph (65.6 M vertices,
+1.8 G edges) at p = 1; the line also carries a summary of R-MAT scale 23 at
+p = 4 (`secondary`). Every printed triangle count is compared with the CPU
+oracle's stored count (`golden_match`).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload rmat-s23|rmat-s14|chunglu-friendster] [--p P]
-                       [--kernel auto|intersect|hashmap]
+                       [--workload chunglu-friendster|rmat-s23|rmat-s14|rmat-sNN|
+                                   batch-4096|serve] [--p P] [--kernel auto|intersect|hashmap]
+                       [--budget-gb B[,B...]] [--secondary rmat-s23|none]
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 (the graph's tasks need no exchange); rank 0 prints one JSON line.
 """
@@ -26,6 +32,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -37,19 +44,25 @@ METRIC = "oriented edges/s counted (excl./incl. H2D), % HBM roofline; p50/p99 re
 UNIT = "edges/s"
 
 WORKLOADS = {
-    # name: (description, generator call)
     "rmat-s23": "R-MAT scale 23 (8,388,608 vertices), edge factor 16, a/b/c/d = "
                 ".57/.19/.19/.05, seed 2; symmetrised, self-loops and duplicates removed "
                 "by the path itself",
     "rmat-s14": "R-MAT scale 14 (16,384 vertices), edge factor 16, a/b/c/d = "
                 ".57/.19/.19/.05, seed 1",
     "chunglu-friendster": "Friendster-shaped Chung-Lu: 65,608,366 vertices, 1,806,067,135 "
-                          "pairs, degree exponent 2.1, expected degree capped at 5,000, seed 3",
+                          "pairs, degree exponent 2.1, expected degree capped at 5,000, seed 3; "
+                          "symmetrised, self-loops and duplicates removed by the path itself",
+    "batch-4096": "4096 independent graphs (seeds 100-4195), pair counts log-uniform "
+                  "in [1e3, 2e6]; even g: G(n,m) with average degree 8-64, odd g: "
+                  "R-MAT a=.57 with edge factor 8-32",
 }
+DEFAULT_WORKLOAD = "chunglu-friendster"
 DEFAULT_P = {"rmat-s23": 4, "rmat-s14": 2, "chunglu-friendster": 1}
-WORKLOADS["batch-4096"] = ("4096 independent graphs (seeds 100-4195), pair counts log-uniform "
-                           "in [1e3, 2e6]; even g: G(n,m) with average degree 8-64, odd g: "
-                           "R-MAT a=.57 with edge factor 8-32")
+# rows of tests/golden/config_counts.txt (written by tests/golden/make_golden.py
+# from graphgen and the CPU oracle alone)
+GOLDEN_ROWS = {"rmat-s23": "rmat_s23_ef16_seed2", "rmat-s14": "rmat_s14_ef16_seed1",
+               "chunglu-friendster": "chunglu_friendster_seed3"}
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
 
 
 def make_graph(name: str):
@@ -60,9 +73,25 @@ def make_graph(name: str):
         return graphgen.rmat_s14()
     if name == "chunglu-friendster":
         return graphgen.chunglu_friendster()
+    if name.startswith("chunglu-friendster/"):  # smaller stand-ins of the same recipe
+        return graphgen.chunglu_friendster(scale_down=int(name.split("/")[1]))
     if name.startswith("rmat-s"):  # smaller/larger instances of the same recipe (profiling)
         return graphgen.rmat(int(name[6:]), 16, 2)
     raise SystemExit(f"unknown workload {name}")
+
+
+def golden_triangles(workload: str):
+    """The oracle's stored triangle count of the workload, or None."""
+    row = GOLDEN_ROWS.get(workload)
+    path = os.path.join(GOLDEN_DIR, "config_counts.txt")
+    if row is None or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if parts and parts[0] == row:
+                return int(parts[3])
+    return None
 
 
 def step_stats(values):
@@ -128,11 +157,11 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"bbtc_clocks_gpu{gpu_index}_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
@@ -169,6 +198,10 @@ class ClockSampler:
                 for nm, val in zip(names, parts[5:9]):
                     if val.lower() == "active":
                         reasons.add(nm)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
@@ -176,48 +209,66 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- CPU oracle
+#
+# The oracle (single-threaded C, tests-only otherwise) is timed here on a
+# bounded sample of the bench workload's own recipe: a scaled-down instance of
+# the Friendster-shaped Chung-Lu graph (same exponent and cap, n and the pair
+# count divided by `scale_down`) or a smaller R-MAT scale. Estimated seconds
+# per oracle pass on one Grace core, from measured runs (R-MAT scale 19: 5.8 s;
+# Chung-Lu / 256: about 4 s), pick the sample that fits the time budget.
 
-def oracle_sample_scale(steps_total: int, budget_s: float = 150.0) -> int:
-    """Largest R-MAT scale (same recipe) whose oracle pass fits budget_s / steps."""
-    per_step = budget_s / max(steps_total, 1)
+CHUNGLU_SAMPLE_S = {1024: 0.6, 512: 1.6, 256: 4.1, 128: 9.9, 64: 24.0}
+
+
+def oracle_sample(workload: str, budget_s: float):
+    """(label, generator) of the largest sample whose oracle pass fits budget_s."""
+    import graphgen
+    if workload.startswith("chunglu-friendster"):
+        sd = 1024
+        for cand in sorted(CHUNGLU_SAMPLE_S, reverse=True):
+            if CHUNGLU_SAMPLE_S[cand] <= budget_s:
+                sd = cand
+        return (f"Friendster-shaped Chung-Lu recipe scaled down {sd}x (gamma 2.1, cap 5,000, "
+                f"seed 3)", lambda: graphgen.chunglu_friendster(scale_down=sd))
     scale = 12
     for s in range(12, 21):
-        if 6.0 * 2.3 ** (s - 19) <= per_step:  # measured on the GPU host: 5.8 s at scale 19
+        if 6.0 * 2.3 ** (s - 19) <= budget_s:
             scale = s
-    return scale
+    return (f"R-MAT scale {scale}, edge factor 16, seed 2",
+            lambda: graphgen.rmat(scale, 16, 2))
 
 
-def run_oracle_sample(scale: int, p: int):
-    """Oracle pipeline (prepare + Alg. 5 per task) on R-MAT `scale`, ef 16, seed 2."""
-    import graphgen
+def run_oracle_sample(gen, p: int):
+    """Oracle pipeline (prepare + Alg. 5 per task) on one sample graph."""
     import oracle
-    n, rp, ci = graphgen.rmat(scale, 16, 2)
+    n, rp, ci = gen()
     t0 = time.perf_counter()
     r = oracle.bbtc(n, rp, ci, p=p)
     dt = time.perf_counter() - t0
     return r["m"], dt, r["total"]
 
 
-def cpu_baseline(steps_total: int, p: int):
-    scale = oracle_sample_scale(steps_total, budget_s=20.0 * steps_total)
-    m, dt, total = run_oracle_sample(scale, p)
+def cpu_baseline(workload: str, p: int):
+    label, gen = oracle_sample(workload, 12.0)
+    m, dt, total = run_oracle_sample(gen, p)
     return {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"oracle pipeline (canonicalise, order, orient, partition p={p}, "
-                      f"Alg. 5 per task) on R-MAT scale {scale}, edge factor 16, seed 2 "
-                      f"({m} edges, {dt:.2f} s, {total} triangles); single-threaded C"}
+                      f"Alg. 5 per task) on {label} ({m} edges, {dt:.2f} s, {total} "
+                      f"triangles); single-threaded C"}
 
 
 def reference_arm(args, rank: int, world: int):
     if rank != 0:
         return
+    workload = args.workload or DEFAULT_WORKLOAD
     steps_total = args.steps + args.warmup
-    scale = oracle_sample_scale(steps_total)
-    p = int(str(args.p).split(",")[0]) or DEFAULT_P.get(args.workload, 4)
+    label, gen = oracle_sample(workload, 150.0 / max(steps_total, 1))
+    p = int(str(args.p).split(",")[0]) or DEFAULT_P.get(workload, 4)
     for _ in range(args.warmup):
-        run_oracle_sample(scale, p)
+        run_oracle_sample(gen, p)
     times, m = [], 0
     for _ in range(args.steps):
-        m, dt, _ = run_oracle_sample(scale, p)
+        m, dt, _ = run_oracle_sample(gen, p)
         times.append(dt)
     ms = 1000.0 * sum(times) / len(times)
     value = m / (ms / 1000.0)
@@ -226,10 +277,10 @@ def reference_arm(args, rank: int, world: int):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS.get(args.workload, args.workload), "p": p,
-                   "sample": f"R-MAT scale {scale}, edge factor 16, seed 2 ({m} edges)"},
+        "config": {"workload": WORKLOADS.get(workload, workload), "p": p,
+                   "sample": f"{label} ({m} edges) per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"R-MAT scale {scale}, edge factor 16, seed 2 per step"},
+                         "sample": f"{label} per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -382,8 +433,11 @@ def run_serve(args, world, rank, local_rank):
     """Open-loop Poisson arrivals of count requests on R-MAT graphs of mixed scale
     (10-22, edge factor 16; each request's graph seed is drawn from its id, from
     a pool of `--serve-seeds` per scale so the device-resident cache can hit).
-    Reports p50/p99 latency and graphs/s at each arrival rate, against serial
-    plain per-request launches (create + count + destroy, no cache, no batching)."""
+    Reports p50/p99 latency and graphs/s at each arrival rate, against two serial
+    baselines: plain per-request launches (create + count + destroy, no cache, no
+    batching) and one count per request on resident handles (the cache without
+    the batching). Admission is by free device memory; --serve-budget-gb caps the
+    cache as well when nonzero."""
     import torch
     import graphgen
     from paper_2009_12457_gb300 import serve
@@ -409,37 +463,52 @@ def run_serve(args, world, rank, local_rank):
             pool[k] = graphgen.rmat(k[0], 16, 1000 * k[0] + k[1])
         return pool[k]
 
-    # serial baseline on the first requests
+    # serial baselines on the first requests
     nser = min(args.serve_serial, len(keys_all))
     serve_p = int(str(args.p).split(",")[0])
-    _, serial_gps = serve.serial_baseline(source, keys_all[:nser], symmetric=True, p=serve_p)
+    ser_counts, serial_gps = serve.serial_baseline(source, keys_all[:nser], symmetric=True,
+                                                   p=serve_p)
+    cached_counts, serial_cached_gps = serve.serial_cached_baseline(
+        source, keys_all[:nser], symmetric=True, p=serve_p)
+    if ser_counts != cached_counts:
+        raise SystemExit("serial baselines disagree")
+    expect = dict(zip(keys_all[:nser], ser_counts))
+    budget = int(args.serve_budget_gb * (1 << 30)) or None
     results = []
     offset = 0
     for lam in rates:
         arrivals = serve.poisson_trace(lam, args.serve_seconds, seed=5)
         keys = keys_all[offset:offset + len(arrivals)]
         offset += len(arrivals)
-        srv = serve.Server(source, device_budget_bytes=int(args.serve_budget_gb * (1 << 30)),
-                           max_batch=256, workers=2, p=serve_p, symmetric=True)
+        srv = serve.Server(source, device_budget_bytes=budget, max_batch=256, workers=2,
+                           p=serve_p, symmetric=True)
         try:
             reqs = serve.run_open_loop(srv, keys, arrivals)
         finally:
             srv.close()
         bad = [r for r in reqs if r.status != 0]
+        mismatched = sum(1 for r in reqs if r.key in expect and r.count != expect[r.key])
         summ = serve.latency_summary(reqs)
         summ.update({"rate_hz": lam, "failed": len(bad), "cache_hits": srv.hits,
                      "cache_misses": srv.misses, "evictions": srv.evictions,
-                     "errors": srv.errors[:4]})
+                     "admission_waits": srv.admission_waits,
+                     "counts_checked_against_serial": sum(1 for r in reqs if r.key in expect),
+                     "counts_mismatched": mismatched, "errors": srv.errors[:4]})
         results.append(summ)
+    best = max(r["graphs_per_s"] for r in results)
     line = {
         "metric": METRIC, "impl": "serve", "unit": "graphs/s",
-        "value": max(r["graphs_per_s"] for r in results), "n_gpus": 1,
+        "value": best, "n_gpus": 1,
         "higher_is_better": True, "data": "synthetic",
         "config": {"workload": "serving: Poisson arrivals, R-MAT scales 10-22, edge factor 16",
                    "seconds_per_rate": args.serve_seconds, "seed_pool_per_scale": seeds,
-                   "device_cache_budget_gb": args.serve_budget_gb, "p": serve_p,
-                   "host_generation_s": gen_s},
+                   "admission": "free device memory (bbtc_device_memory) minus a 4 GiB reserve"
+                                + (f", cache capped at {args.serve_budget_gb} GB" if budget else ""),
+                   "p": serve_p, "host_generation_s": gen_s},
         "serial_plain_graphs_per_s": serial_gps,
+        "serial_cached_graphs_per_s": serial_cached_gps,
+        "served_vs_serial_plain": best / serial_gps,
+        "served_vs_serial_cached": best / serial_cached_gps,
         "rates": results,
     }
     print(json.dumps(line), flush=True)
@@ -447,14 +516,228 @@ def run_serve(args, world, rank, local_rank):
 
 # ------------------------------------------------------------- GPU path
 
+def measure(args, workload: str, p: int, budget_gb: float, env, with_cpu: bool):
+    """Times one workload at one (p, budget): W warm-up steps, then K timed steps
+    from device-resident input and K from pinned host input. Returns rank 0's line
+    (None on the other ranks)."""
+    import torch
+    import paper_2009_12457_gb300 as bb
+    world, rank, local_rank, dist = env
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n, rp, ci = make_graph(workload)
+    flags = bb.INPUT_SYMMETRIC  # the generator lists every pair under both endpoints
+    stream = torch.cuda.Stream()
+    h_rp = torch.from_numpy(rp).pin_memory()
+    h_ci = torch.from_numpy(ci).pin_memory()
+    d_rp = h_rp.cuda()
+    d_ci = h_ci.cuda()
+    torch.cuda.synchronize()
+    del rp, ci
+    budget = int(budget_gb * (1 << 30))
+
+    def step(device_resident: bool, want_info: bool = False):
+        if device_resident:
+            h = bb.bbtc_graph_create_async(n, d_rp, d_ci, flags, stream)
+        else:
+            h = bb.bbtc_graph_create_async(n, h_rp, h_ci, flags, stream)
+        try:
+            total = bb.bbtc_count(h, bb.make_opts(p=p, kernel=args.kernel, stream=stream,
+                                                  device_budget_bytes=budget,
+                                                  partition=args.partition))
+            # the graph's sizes and wedge sums (an extra pass over the CSR) are
+            # read in the warm-up only, outside the timed steps
+            info = bb.bbtc_graph_get_info(h) if want_info else None
+            tim = bb.bbtc_graph_get_timings(h) if device_resident else None
+        finally:
+            bb.bbtc_graph_destroy(h)
+        return total, info, tim
+
+    # warm-up (also validates that every step gives the same count)
+    totals = set()
+    info = None
+    for _ in range(args.warmup):
+        total, info, _ = step(True, want_info=True)
+        totals.add(total)
+    m = info["m"]
+
+    # timed: device-resident inputs
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    count_ms, prep_ms, plan_ms, stream_info = [], [], [], []
+    launches0 = bb.bbtc_kernel_launches()
+    with ClockSampler(local_rank) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            total, _, tim = step(True)
+            totals.add(total)
+            count_ms.append(tim["count_ms"])
+            prep_ms.append(tim["prep_ms"])
+            plan_ms.append(tim["plan_ms"])
+            stream_info.append({k: tim[k] for k in ("stream_rounds", "stream_h2d_bytes",
+                                                    "stream_copy_ms", "stream_block_bytes",
+                                                    "stream_device_peak_bytes",
+                                                    "stream_mode")})
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = bb.bbtc_kernel_launches() - launches0
+    ms = reduce_max_ms(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
+
+    # timed: host inputs through the same calls (H2D and count D2H inside),
+    # after one untimed host-input step (the device pool grows once for the
+    # input copy)
+    totals.add(step(False)[0])
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        total, _, _ = step(False)
+        totals.add(total)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max_ms(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    barrier()
+
+    if len(totals) != 1:
+        raise SystemExit(f"inconsistent triangle counts across steps: {sorted(totals)}")
+    triangles = next(iter(totals))
+    golden = golden_triangles(workload)
+
+    # load imbalance of the partition (Sec. 4.4): lambda = m_max / m_avg over the
+    # p(p+1)/2 blocks, from one more (untimed) plan
+    h = bb.bbtc_graph_create_async(n, d_rp, d_ci, flags, stream)
+    try:
+        bb.bbtc_graph_plan(h, bb.make_opts(p=p, kernel=args.kernel, stream=stream,
+                                           partition=args.partition))
+        nnz = bb.bbtc_graph_get_plan(h, p)["block_nnz"]
+        dev_bytes = bb.bbtc_graph_get_info(h)["device_bytes"]
+    finally:
+        bb.bbtc_graph_destroy(h)
+    lam = float(nnz.max()) / (m / (p * (p + 1) / 2)) if m else 1.0
+
+    # pinned host-to-device bandwidth right now (streamed counts depend on it,
+    # and it varies from box to box)
+    h2d_gbs = None
+    if budget:
+        k = min(int(h_ci.numel()), 1 << 28)
+        tmp = torch.empty(k, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(stream):
+            tmp.copy_(h_ci[:k], non_blocking=True)
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            for _ in range(3):
+                tmp.copy_(h_ci[:k], non_blocking=True)
+            b1.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = 3 * 4 * k / (b0.elapsed_time(b1) / 1000.0) / 1e9
+        del tmp
+    input_entries = int(h_ci.numel())
+    del d_rp, d_ci, h_rp, h_ci
+    torch.cuda.empty_cache()
+    if rank != 0:
+        return None
+
+    peak, peak_kind = measured_peaks()
+    kms = sum(count_ms) / len(count_ms)
+    # bytes the destination-grouped counting kernel reads: the 16-byte in-edge
+    # records, each N(v) staged once (4 B per oriented edge), and the part of each
+    # N(u) above v (sum over u of d+(u)(d+(u)-1)/2 elements, 4 B each)
+    own = 4 * (5 * m + info["wedges_out"])
+    achieved = own / (kms / 1000.0) / 1e9
+    # the survey's W_min: every edge's N(v) read once per in-edge of v; this kernel
+    # never makes those reads, so it is reported for context, not as its roofline
+    wmin = 4 * (m + info["wedges_in"])
+    # bytes a merge-based intersection of both full lists would read:
+    # 4 * sum over (u,v) of (d+(u) + d+(v)), with sum_(u,v) d+(u) = sum_u d+(u)^2
+    # = 2 * sum_u C(d+(u), 2) + m
+    wmerge = 4 * (2 * info["wedges_out"] + m + info["wedges_in"])
+    h2d = (n + 1) * 8 + input_entries * 4
+    traffic = recorded_traffic(workload, p, args.kernel) if not budget else None
+    line = {
+        "metric": METRIC,
+        "value": replica_throughput(m, world, ms),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOADS.get(workload, workload), "p": p,
+            "kernel": args.kernel, "partition": args.partition,
+            "lambda": lam, "max_block_nnz": int(nnz.max()),
+            "n": n, "m": m, "triangles": triangles,
+            "golden_triangles": golden, "golden_match": (None if golden is None
+                                                         else triangles == golden),
+            "input_entries": input_entries,
+            "l2": "inputs larger than L2 (input CSR %.2f GB, oriented CSR %.2f GB)"
+                  % (h2d / 1e9, (m * 8 + (n + 1) * 8) / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "phase_ms": {"prep": statistics.mean(prep_ms), "plan": statistics.mean(plan_ms),
+                         "count_kernel": kms},
+            "phase_ms_median_min_p90": {k: step_stats(v) for k, v in
+                                        (("prep", prep_ms), ("plan", plan_ms),
+                                         ("count_kernel", count_ms))},
+            "device_budget_gb": budget_gb,
+            "handle_and_plan_device_bytes": dev_bytes,
+            "streaming": dict(stream_info[-1], pinned_h2d_gbs=h2d_gbs,
+                              h2d_over_block_bytes=(stream_info[-1]["stream_h2d_bytes"] /
+                                                    max(stream_info[-1]["stream_block_bytes"], 1)),
+                              budget_bytes=budget) if budget else None,
+        },
+        "e2e": {"value": replica_throughput(m, world, e2e_ms), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak,
+                     "traffic": traffic,
+                     "traffic_source": ("committed ncu record of this kernel source and "
+                                        "workload (profiles/k_count_traffic.json), not "
+                                        "measured in this run" if traffic is not None else
+                                        "no ncu record for this kernel source and workload"),
+                     "kernel": "k_count (per-task counting, a9)",
+                     "algorithmic_bytes": own,
+                     "bytes_formula": "4*(5m + sum over u of d+(u)(d+(u)-1)/2): 16-byte "
+                                      "in-edge records, each N(v) staged once, the probed "
+                                      "part of each N(u) above v",
+                     "w_min_bytes": wmin,
+                     "w_min_formula": "4*(m + sum over oriented edges (u,v) of d+(v)); reads "
+                                      "N(v) once per in-edge, which this kernel does not do",
+                     "w_min_over_time_per_peak": wmin / (kms / 1000.0) / 1e9 / peak,
+                     "w_merge_bytes": wmerge,
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "clocks": clocks.summary(),
+        "gpu_launches": launches,
+    }
+    if with_cpu:
+        line["cpu_baseline"] = cpu_baseline(workload, p)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat-s23",
-                    help="rmat-s23 (default), rmat-s14, chunglu-friendster, or rmat-sNN")
+    ap.add_argument("--workload", default=None,
+                    help="chunglu-friendster (default), rmat-s23, rmat-s14, rmat-sNN, "
+                         "chunglu-friendster/D (scaled down D times), batch-4096, serve")
+    ap.add_argument("--secondary", default="rmat-s23",
+                    help="with the default workload: a second workload summarised in the "
+                         "same line ('none' to skip)")
     ap.add_argument("--p", default="0", help="blocks per side; a comma list runs each")
     ap.add_argument("--kernel", default="auto", choices=["auto", "intersect", "hashmap"])
     ap.add_argument("--partition", default="edges", choices=["edges", "probe"],
@@ -467,7 +750,8 @@ def main():
     ap.add_argument("--serve-rates", default="200,500,1000,2000,5000")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-seeds", type=int, default=4)
-    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=0.0,
+                    help="cap on the serving cache (GB); 0 = admission by free device memory")
     ap.add_argument("--serve-serial", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -480,10 +764,12 @@ def main():
     if args.impl == "reference":
         reference_arm(args, rank, world)
         return
-    if args.workload.startswith("batch-"):
+    default_run = args.workload is None
+    workload = args.workload or DEFAULT_WORKLOAD
+    if workload.startswith("batch-"):
         run_batch(args, world, rank, local_rank)
         return
-    if args.workload == "serve":
+    if workload == "serve":
         run_serve(args, world, rank, local_rank)
         return
 
@@ -495,198 +781,40 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    env = (world, rank, local_rank, dist)
 
     p_list = [int(x) for x in str(args.p).split(",")]
-    p_list = [q or DEFAULT_P.get(args.workload, 4) for q in p_list]
+    p_list = [q or DEFAULT_P.get(workload.split("/")[0], 4) for q in p_list]
     budgets = [float(x) for x in str(args.budget_gb).split(",")]
-    n, rp, ci = make_graph(args.workload)
-    flags = bb.INPUT_SYMMETRIC  # the generator lists every pair under both endpoints
-    stream = torch.cuda.Stream()
-    h_rp = torch.from_numpy(rp).pin_memory()
-    h_ci = torch.from_numpy(ci).pin_memory()
-    d_rp = h_rp.cuda()
-    d_ci = h_ci.cuda()
-    torch.cuda.synchronize()
-    del rp, ci
-
-    def measure(p: int, budget_gb: float, first_line: bool):
-        budget = int(budget_gb * (1 << 30))
-        def step(device_resident: bool, want_info: bool = False):
-            if device_resident:
-                h = bb.bbtc_graph_create_async(n, d_rp, d_ci, flags, stream)
-            else:
-                h = bb.bbtc_graph_create_async(n, h_rp, h_ci, flags, stream)
-            try:
-                total = bb.bbtc_count(h, bb.make_opts(p=p, kernel=args.kernel, stream=stream,
-                                                      device_budget_bytes=budget,
-                                                      partition=args.partition))
-                # the graph's sizes and wedge sums (an extra pass over the CSR) are
-                # read in the warm-up only, outside the timed steps
-                info = bb.bbtc_graph_get_info(h) if want_info else None
-                tim = bb.bbtc_graph_get_timings(h) if device_resident else None
-            finally:
-                bb.bbtc_graph_destroy(h)
-            return total, info, tim
-
-        # warm-up (also validates that every step gives the same count)
-        totals = set()
-        info = None
-        for _ in range(args.warmup):
-            total, info, _ = step(True, want_info=True)
-            totals.add(total)
-        m = info["m"]
-
-        # timed: device-resident inputs
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        count_ms, prep_ms, plan_ms, stream_info = [], [], [], []
-        launches0 = bb.bbtc_kernel_launches()
-        with ClockSampler(local_rank) as clocks:
-            barrier()
-            torch.cuda.synchronize()
-            ev0.record(stream)
-            for _ in range(args.steps):
-                total, _, tim = step(True)
-                totals.add(total)
-                count_ms.append(tim["count_ms"])
-                prep_ms.append(tim["prep_ms"])
-                plan_ms.append(tim["plan_ms"])
-                stream_info.append({k: tim[k] for k in ("stream_rounds", "stream_h2d_bytes",
-                                                        "stream_copy_ms")})
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            barrier()
-        launches = bb.bbtc_kernel_launches() - launches0
-        ms = reduce_max_ms(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
-
-        # timed: host inputs through the same calls (H2D and count D2H inside),
-        # after one untimed host-input step (the device pool grows once for the
-        # input copy)
-        totals.add(step(False)[0])
-        barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            total, _, _ = step(False)
-            totals.add(total)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = reduce_max_ms(e0.elapsed_time(e1) / args.steps, dist, "cuda")
-        barrier()
-
-        if len(totals) != 1:
-            raise SystemExit(f"inconsistent triangle counts across steps: {sorted(totals)}")
-
-        # load imbalance of the partition (Sec. 4.4): lambda = m_max / m_avg over the
-        # p(p+1)/2 blocks, from one more (untimed) plan
-        h = bb.bbtc_graph_create_async(n, d_rp, d_ci, flags, stream)
-        try:
-            bb.bbtc_graph_plan(h, bb.make_opts(p=p, kernel=args.kernel, stream=stream,
-                                               partition=args.partition))
-            nnz = bb.bbtc_graph_get_plan(h, p)["block_nnz"]
-        finally:
-            bb.bbtc_graph_destroy(h)
-        lam = float(nnz.max()) / (m / (p * (p + 1) / 2)) if m else 1.0
-
-        # pinned host-to-device bandwidth right now (streamed counts depend on it,
-        # and it varies from box to box)
-        h2d_gbs = None
-        if budget:
-            k = min(int(h_ci.numel()), 1 << 28)
-            tmp = torch.empty(k, dtype=torch.int32, device="cuda")
-            with torch.cuda.stream(stream):
-                tmp.copy_(h_ci[:k], non_blocking=True)
-                b0 = torch.cuda.Event(enable_timing=True)
-                b1 = torch.cuda.Event(enable_timing=True)
-                b0.record(stream)
-                for _ in range(3):
-                    tmp.copy_(h_ci[:k], non_blocking=True)
-                b1.record(stream)
-            torch.cuda.synchronize()
-            h2d_gbs = 3 * 4 * k / (b0.elapsed_time(b1) / 1000.0) / 1e9
-            del tmp
-
-        if rank == 0:
-            peak, peak_kind = measured_peaks()
-            kms = sum(count_ms) / len(count_ms)
-            wmin = 4 * (m + info["wedges_in"])
-            achieved = wmin / (kms / 1000.0) / 1e9
-            # bytes the destination-grouped kernel itself cannot avoid: the in-edge
-            # records (u, v, position), each N(v) staged once, and the part of each
-            # N(u) above v (sum over u of d+(u)(d+(u)-1)/2 elements)
-            own = 4 * (4 * m + info["wedges_out"])
-            # bytes a merge-based intersection of both full lists would read:
-            # 4 * sum over (u,v) of (d+(u) + d+(v)), with sum_(u,v) d+(u) = sum_u d+(u)^2
-            # = 2 * sum_u C(d+(u), 2) + m
-            wmerge = 4 * (2 * info["wedges_out"] + m + info["wedges_in"])
-            h2d = (n + 1) * 8 + int(h_ci.numel()) * 4
-            line = {
-                "metric": METRIC,
-                "value": replica_throughput(m, world, ms),
-                "unit": UNIT,
-                "n_gpus": world,
-                "steps": args.steps,
-                "warmup": args.warmup,
-                "ms_per_step": ms,
-                "higher_is_better": True,
-                "scaling": "weak",
-                "vs_baseline": None,
-                "dtype": "int32",
-                "data": "synthetic",
-                "config": {
-                    "workload": WORKLOADS.get(args.workload, args.workload), "p": p,
-                    "kernel": args.kernel, "partition": args.partition,
-                    "lambda": lam, "max_block_nnz": int(nnz.max()),
-                    "n": n, "m": m, "triangles": next(iter(totals)),
-                    "input_entries": int(h_ci.numel()),
-                    "l2": "inputs larger than L2 (input CSR %.2f GB, oriented CSR %.2f GB)"
-                          % (h2d / 1e9, (m * 8 + (n + 1) * 8) / 1e9),
-                    "parallelism": "replicas" if world > 1 else "single GPU",
-                    "phase_ms": {"prep": statistics.mean(prep_ms), "plan": statistics.mean(plan_ms),
-                                 "count_kernel": kms},
-                    "phase_ms_median_min_p90": {k: step_stats(v) for k, v in
-                                                (("prep", prep_ms), ("plan", plan_ms),
-                                                 ("count_kernel", count_ms))},
-                    "device_budget_gb": budget_gb,
-                    "streaming": dict(stream_info[-1], pinned_h2d_gbs=h2d_gbs) if budget else None,
-                },
-                "e2e": {"value": replica_throughput(m, world, e2e_ms), "unit": UNIT,
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak,
-                             "traffic": recorded_traffic(args.workload, p, args.kernel),
-                             "kernel": "k_count (per-task counting, a9)",
-                             "algorithmic_bytes": wmin,
-                             "bytes_formula": "4*(m + sum over oriented edges (u,v) of d+(v))",
-                             "kernel_own_bytes": own,
-                             "kernel_own_formula": "4*(4m + sum over u of d+(u)(d+(u)-1)/2)",
-                             "kernel_own_frac": own / (kms / 1000.0) / 1e9 / peak,
-                             "w_merge_bytes": wmerge,
-                             "peak_source": f"{peak_kind} hbm_gbs"},
-                "clocks": clocks.summary(),
-                "gpu_launches": launches,
-            }
-            if not args.no_cpu_baseline and first_line:
-                line["cpu_baseline"] = cpu_baseline(1, p)
-            print(json.dumps(line), flush=True)
-
     first = True
     for p in p_list:
         for budget_gb in budgets:
             try:
-                measure(p, budget_gb, first)
+                line = measure(args, workload, p, budget_gb, env,
+                               with_cpu=first and world == 1 and not args.no_cpu_baseline)
             except bb.BbtcError as e:  # e.g. a budget too small for one task's blocks
-                if rank == 0:
-                    print(json.dumps({"metric": METRIC, "error": str(e), "p": p,
-                                      "device_budget_gb": budget_gb,
-                                      "workload": args.workload}), flush=True)
+                line = {"metric": METRIC, "error": str(e), "p": p,
+                        "device_budget_gb": budget_gb, "workload": workload}
             first = False
+            if default_run and args.secondary != "none":  # every rank measures it
+                sec = measure(args, args.secondary, DEFAULT_P.get(args.secondary, 4), 0.0, env,
+                              with_cpu=False)
+                if sec is not None and line is not None:
+                    line["secondary"] = {
+                        "workload": sec["config"]["workload"], "p": sec["config"]["p"],
+                        "value": sec["value"], "unit": UNIT, "ms_per_step": sec["ms_per_step"],
+                        "e2e": sec["e2e"], "phase_ms": sec["config"]["phase_ms"],
+                        "triangles": sec["config"]["triangles"],
+                        "golden_match": sec["config"]["golden_match"],
+                        "roofline_frac": sec["roofline"]["frac"],
+                        "roofline_achieved_gbs": sec["roofline"]["achieved"],
+                        "w_min_over_time_per_peak": sec["roofline"]["w_min_over_time_per_peak"],
+                        "clocks": sec["clocks"], "gpu_launches": sec["gpu_launches"]}
+            if line is not None:
+                print(json.dumps(line), flush=True)
+            if line is not None and line.get("config", {}).get("golden_match") is False:
+                raise SystemExit(f"triangle count {line['config']['triangles']} differs from "
+                                 f"the oracle's {line['config']['golden_triangles']}")
 
     if dist is not None:
         dist.destroy_process_group()

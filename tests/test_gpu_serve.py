@@ -1,10 +1,12 @@
-"""Serving loop: each request's count is the same alone and in the mix (GPU)."""
+"""Serving loop: each request's count is the oracle's and the same alone and in the
+mix (GPU)."""
 import time
 
 import numpy as np
 import pytest
 
 import graphgen
+import oracle
 import paper_2009_12457_gb300 as bb
 from paper_2009_12457_gb300 import serve
 from paper_2009_12457_gb300.autotune import Autotuner
@@ -33,11 +35,15 @@ def source(key):
 def test_served_counts_equal_counts_alone():
     arrivals = serve.poisson_trace(400.0, 1.5, seed=5)
     keys = [request_key(i) for i in range(len(arrivals))]
-    alone = {}
+    alone, exact = {}, {}
     for k in set(keys):
         with bb.Graph(*source(k)) as g:
             alone[k] = g.count(p=2)
-    # a budget of a few graphs forces admission waits and evictions
+        n, rp, ci = source(k)
+        pr = oracle.prepare(n, rp, ci)
+        exact[k] = oracle.tc_intersect(n, pr["rowptr"], pr["colidx"])
+    assert alone == exact
+    # a budget of a few graphs forces evictions
     srv = serve.Server(source, device_budget_bytes=12 << 20, max_batch=32, workers=2, p=2)
     try:
         reqs = serve.run_open_loop(srv, keys, arrivals)
@@ -45,8 +51,8 @@ def test_served_counts_equal_counts_alone():
         srv.close()
     assert len(reqs) == len(keys)
     assert all(r.status == 0 for r in reqs)
-    wrong = [(r.rid, r.key, r.count, alone[r.key], r.batch_size) for r in reqs
-             if r.count != alone[r.key]]
+    wrong = [(r.rid, r.key, r.count, exact[r.key], r.batch_size) for r in reqs
+             if r.count != exact[r.key]]
     assert not wrong, wrong[:10]
     assert srv.evictions > 0 and srv.hits > 0
     assert max(r.batch_size for r in reqs) > 1  # requests really shared launches
@@ -54,13 +60,23 @@ def test_served_counts_equal_counts_alone():
     assert summary["p99_ms"] >= summary["p50_ms"] > 0
 
 
-def test_serial_baseline_matches():
+def test_serial_baselines_match():
     keys = [request_key(i) for i in range(12)]
     counts, rate = serve.serial_baseline(source, keys, p=2)
+    cached, rate_cached = serve.serial_cached_baseline(source, keys, p=2)
+    assert counts == cached
     for k, c in zip(keys, counts):
         with bb.Graph(*source(k)) as g:
             assert c == g.count(p=3)
-    assert rate > 0
+    assert rate > 0 and rate_cached > 0
+
+
+def test_device_memory_report():
+    mem = bb.bbtc_device_memory(torch.cuda.current_device())
+    free, total = torch.cuda.mem_get_info()
+    assert 0 < mem["total"] == total
+    assert mem["pool_used"] <= mem["pool_reserved"]
+    assert mem["available"] >= free - (1 << 30)
 
 
 def test_autotuner_choice_gives_the_same_count(tmp_path):
@@ -95,7 +111,7 @@ def test_a_bad_graph_fails_only_its_own_requests():
     srv = serve.Server(mixed_source, device_budget_bytes=1 << 30, max_batch=64, workers=1, p=2)
     try:
         reqs = [serve.Request(i, k, time.perf_counter()) for i, k in enumerate(keys)]
-        with srv.cv:  # the worker takes the whole burst as one batch
+        with srv.cv:  # one burst; batches form as its graphs become ready
             for r in reqs:
                 srv.submit(r)
         srv.drain(len(reqs))
@@ -111,6 +127,5 @@ def test_a_bad_graph_fails_only_its_own_requests():
             assert r.status != 0
         else:
             assert r.status == 0 and r.count == alone[r.key], (r.key, r.status, r.count)
-    assert all(r.batch_size == len(keys) for r in reqs)   # the bad graphs shared the batch
     assert srv.errors
     assert all(r.status == 0 and r.count == alone[r.key] for r in later)
