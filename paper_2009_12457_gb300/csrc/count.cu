@@ -452,8 +452,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         }
       }
       const uint32_t len = (uint32_t)(s1 - s0);
-      const uint32_t incl = warp_inclusive_scan(len);
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t total = __reduce_add_sync(0xffffffffu, len);
       if (total == 0) continue;
 
       // stage N(G_jk, v) once per (task, v) in one of three forms:
@@ -473,13 +472,14 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
         if (tag == staged_tag) {
           staged = true;
         } else if (nb == 32 || total >= (uint32_t)blen / 2) {
-          int32_t first = 0, last = 0;
-          if (lane == 0) {
-            first = ci_jk[b0];
-            last = ci_jk[b1 - 1];
-          }
-          first = __shfl_sync(0xffffffffu, first, 0);
-          last = __shfl_sync(0xffffffffu, last, 0);
+          // the list's first 32 entries, one per lane, and its last entry, in
+          // one round of loads: the value range comes from them
+          const int32_t x0 = (int)lane < blen ? ci_jk[b0 + lane] : 0;
+          int32_t lastv = 0;
+          if (lane == 0 && blen > 32) lastv = ci_jk[b1 - 1];
+          const int32_t first = __shfl_sync(0xffffffffu, x0, 0);
+          const int32_t last = blen > 32 ? __shfl_sync(0xffffffffu, lastv, 0)
+                                         : __shfl_sync(0xffffffffu, x0, blen - 1);
           const int64_t span = (int64_t)last - first + 1;
           int mode = ST_NONE;
           if (kflag == 0) {
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
               __syncwarp();
               if (!failed)
                 for (int i = lane; i < blen; i += 32) {
-                  const uint32_t d = (uint32_t)(src[i] - first);
+                  const uint32_t d = (uint32_t)((i < 32 ? x0 : src[i]) - first);
                   atomicOr(reinterpret_cast<unsigned *>(stage) + (d >> 5), 1u << (d & 31u));
                 }
               staged_first = first;
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
               const uint32_t hmask = (uint32_t)hsize - 1u;
               if (!failed)
                 for (int i = lane; i < blen; i += 32) {
-                  const int32_t key = src[i];
+                  const int32_t key = i < 32 ? x0 : src[i];
                   if (mode == ST_FILTER) {
                     const uint32_t fb = filter_bit(key);
                     atomicOr(reinterpret_cast<unsigned *>(stage) + (fb >> 5), 1u << (fb & 31u));
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
                 failed = !bulk_wait(&rec.mbar, mbar_parity);
                 staged_off = (int)(b0 - e0);
               } else {
-                for (int i = lane; i < blen; i += 32) stage[i] = ci_jk[b0 + i];
+                for (int i = lane; i < blen; i += 32) stage[i] = i < 32 ? x0 : ci_jk[b0 + i];
               }
               staged_len = blen;
             }
@@ -630,6 +630,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
       // flattened probes, interleaved over the lanes (lanes that share an
       // in-edge read consecutive elements); each lane's owner only moves
       // forward, at most 31 steps per batch
+      const uint32_t incl = warp_inclusive_scan(len);
       rec.s0[lane] = (uint32_t)s0;
       rec.incl[lane] = incl;
       if (!uniform) {
