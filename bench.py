@@ -239,9 +239,10 @@ def oracle_sample(workload: str, budget_s: float):
 
 
 def run_oracle_sample(gen, p: int):
-    """Oracle pipeline (prepare + Alg. 5 per task) on one sample graph."""
+    """Oracle pipeline (prepare + Alg. 5 per task) on one sample graph; `gen` is a
+    generator callable or an already generated (n, rowptr, colidx)."""
     import oracle
-    n, rp, ci = gen()
+    n, rp, ci = gen() if callable(gen) else gen
     t0 = time.perf_counter()
     r = oracle.bbtc(n, rp, ci, p=p)
     dt = time.perf_counter() - t0
@@ -264,11 +265,12 @@ def reference_arm(args, rank: int, world: int):
     steps_total = args.steps + args.warmup
     label, gen = oracle_sample(workload, 150.0 / max(steps_total, 1))
     p = int(str(args.p).split(",")[0]) or DEFAULT_P.get(workload, 4)
+    graph = gen()  # generated once; each step times the oracle on it
     for _ in range(args.warmup):
-        run_oracle_sample(gen, p)
+        run_oracle_sample(graph, p)
     times, m = [], 0
     for _ in range(args.steps):
-        m, dt, _ = run_oracle_sample(gen, p)
+        m, dt, _ = run_oracle_sample(graph, p)
         times.append(dt)
     ms = 1000.0 * sum(times) / len(times)
     value = m / (ms / 1000.0)
@@ -402,6 +404,18 @@ def run_batch(args, world, rank, local_rank):
     torch.cuda.synchronize()
     e2e_ms = q0.elapsed_time(q1) / args.steps
 
+    # every graph's count against the oracle's stored value (the first ng of 4096)
+    golden_path = os.path.join(GOLDEN_DIR, "batch4096_counts.txt")
+    golden_match = None
+    if os.path.exists(golden_path):
+        want = {}
+        with open(golden_path) as f:
+            for row in f:
+                if row.strip() and not row.startswith("#"):
+                    g_, _, _, tri = (int(x) for x in row.split())
+                    want[g_] = tri
+        if all(g_ in want for g_ in range(ng)):
+            golden_match = bool(all(int(ref[g_]) == want[g_] for g_ in range(ng)))
     peak, peak_kind = measured_peaks()
     line = {
         "metric": METRIC, "value": m_total / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
@@ -412,7 +426,8 @@ def run_batch(args, world, rank, local_rank):
                                              f"{ng} independent graphs (seeds 100-{99 + ng}), "
                                              "the first of the 4096-graph recipe"),
                    "graphs": ng, "m_total": m_total,
-                   "triangles_total": int(ref.sum()), "autotuned": choice,
+                   "triangles_total": int(ref.sum()), "golden_match": golden_match,
+                   "autotuned": choice,
                    "l2": "inputs larger than L2 (%.2f GB)" % (colidx.nbytes / 1e9)},
         "batched_vs_plain": {"plain_ms_per_step": plain_ms, "batched_ms_per_step": ms,
                              "speedup": plain_ms / ms,
@@ -425,6 +440,8 @@ def run_batch(args, world, rank, local_rank):
         "peak_hbm_gbs": {"value": peak, "source": peak_kind},
     }
     print(json.dumps(line), flush=True)
+    if golden_match is False:
+        raise SystemExit("batched per-graph counts differ from the oracle's stored counts")
 
 
 # ------------------------------------------------------------ serving form
