@@ -568,7 +568,7 @@ def measure(args, workload: str, p: int, budget_gb: float, env, with_cpu: bool):
             # the graph's sizes and wedge sums (an extra pass over the CSR) are
             # read in the warm-up only, outside the timed steps
             info = bb.bbtc_graph_get_info(h) if want_info else None
-            tim = bb.bbtc_graph_get_timings(h) if device_resident else None
+            tim = bb.bbtc_graph_get_timings(h)
         finally:
             bb.bbtc_graph_destroy(h)
         return total, info, tim
@@ -614,12 +614,18 @@ def measure(args, workload: str, p: int, budget_gb: float, env, with_cpu: bool):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    e2e_phase = {"prep": [], "plan": [], "count_kernel": []}
+    w0 = time.perf_counter()
     e0.record(stream)
     for _ in range(args.steps):
-        total, _, _ = step(False)
+        total, _, tim = step(False)
         totals.add(total)
+        e2e_phase["prep"].append(tim["prep_ms"])
+        e2e_phase["plan"].append(tim["plan_ms"])
+        e2e_phase["count_kernel"].append(tim["count_ms"])
     e1.record(stream)
     torch.cuda.synchronize()
+    e2e_wall_ms = 1000.0 * (time.perf_counter() - w0) / args.steps
     e2e_ms = reduce_max_ms(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     barrier()
 
@@ -716,7 +722,9 @@ def measure(args, workload: str, p: int, budget_gb: float, env, with_cpu: bool):
                               budget_bytes=budget) if budget else None,
         },
         "e2e": {"value": replica_throughput(m, world, e2e_ms), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
+                "ms_per_step": e2e_ms, "host_wall_ms_per_step": e2e_wall_ms,
+                "phase_ms": {k: statistics.mean(v) for k, v in e2e_phase.items()}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": traffic,

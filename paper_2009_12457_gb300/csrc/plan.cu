@@ -192,6 +192,137 @@ __global__ void __launch_bounds__(IE_NT_S) k_inedge_scatter(const int64_t *__res
   }
 }
 
+// Two-phase in-edge build for large parts. A direct scatter writes each
+// 16-byte record to a random slot: half a 32-byte sector, read and written
+// back whole, with a random counter per edge (on the Friendster-shaped graph
+// the scatter moves 4x its algorithmic bytes). Instead:
+//  1. partition: each CTA takes tiles of IEB_T edges, builds their records,
+//     buckets them in shared memory into IEB_B destination ranges of about
+//     equal record count, reserves each bucket's share with one atomic and
+//     writes it as one contiguous run into the bucket's own range of the
+//     output positions (in a temporary array);
+//  2. place: a grid-stride pass reads the temporary array in order and puts
+//     each record at its destination's cursor. The CTAs move through the
+//     buckets together, so the bucket being filled (tens of MB) and its
+//     cursors stay in L2 and its lines go to HBM once, whole.
+constexpr int IEB_T = 4096;   // edges per partition tile
+constexpr int IEB_NT = 512;   // threads of a partition CTA (8 edges each)
+constexpr int IEB_B = 512;    // buckets (one per partition thread in the scan)
+constexpr int64_t IEB_MIN_EDGES = 16ll << 20;  // smaller parts use the direct scatter
+static_assert(IEB_NT == IEB_B && IEB_T == 8 * IEB_NT, "partition layout");
+
+// Bucket b of part a holds the destinations [bnd[b], bnd[b+1]) (relative to
+// c_a) whose in-edge offsets start in [ceil(b M / B), ceil((b+1) M / B)), M the
+// part's edge count; their records take the output offsets [bstart[b],
+// bstart[b+1]). scan holds the exclusive scan of the bins destinations' counts.
+__global__ void k_ieb_bounds(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ cuts,
+                             int a, const uint64_t *__restrict__ scan, int64_t bins,
+                             int32_t *__restrict__ bnd, unsigned *__restrict__ bstart,
+                             unsigned *__restrict__ bcur) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > IEB_B) return;
+  const int64_t M = rowptr[cuts[a + 1]] - rowptr[cuts[a]];
+  int64_t idx = bins;
+  if (b == 0) {
+    idx = 0;
+  } else if (b < IEB_B) {
+    const uint64_t target = (uint64_t)((M * b + IEB_B - 1) / IEB_B);
+    idx = lower_bound_dev<uint64_t, int64_t>(scan, 0, bins, target);
+  }
+  bnd[b] = (int32_t)idx;
+  bstart[b] = (unsigned)(idx < bins ? scan[idx] : (uint64_t)M);
+  if (b < IEB_B) bcur[b] = 0;
+}
+
+__global__ void __launch_bounds__(IEB_NT, 2)
+    k_ieb_partition(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                    const int32_t *__restrict__ esrc, const int32_t *__restrict__ cuts_g, int a,
+                    int p, const uint32_t *__restrict__ spl_a, const int32_t *__restrict__ bnd_g,
+                    const unsigned *__restrict__ bstart, unsigned *__restrict__ bcur,
+                    InEdge *__restrict__ tmp) {
+  __shared__ int32_t bnd[IEB_B + 1];
+  __shared__ unsigned cnt[IEB_B], loff[IEB_B], gbase[IEB_B];
+  __shared__ unsigned scan_tmp[IEB_NT / 32 + 1];
+  __shared__ int32_t cuts[MAXP + 1];
+  __shared__ uint16_t sb[IEB_T];  // bucket of each staged slot
+  extern __shared__ __align__(16) unsigned char ieb_smem[];
+  InEdge *stage = reinterpret_cast<InEdge *>(ieb_smem);  // IEB_T records
+  for (int i = threadIdx.x; i <= IEB_B; i += IEB_NT) bnd[i] = bnd_g[i];
+  for (int i = threadIdx.x; i <= p; i += IEB_NT) cuts[i] = cuts_g[i];
+  const int32_t c_a = cuts_g[a];
+  const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts_g[a + 1]];
+  __syncthreads();
+  for (int64_t t0 = e0 + (int64_t)blockIdx.x * IEB_T; t0 < e1; t0 += (int64_t)gridDim.x * IEB_T) {
+    const int nv = (int)(e1 - t0 < IEB_T ? e1 - t0 : IEB_T);
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    InEdge r[8];
+    int bk[8];
+    unsigned lr[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = (int)threadIdx.x + k * IEB_NT;
+      bk[k] = -1;
+      if (i < nv) {
+        const int64_t idx = t0 + i;
+        const int32_t v = colidx[idx];
+        const int32_t u = esrc[idx];
+        const int b = part_of_dev(cuts, p, v);  // >= a: v > u
+        const uint32_t f = spl_a[(int64_t)(u - c_a) * (p - a + 1) + (b - a + 1)];
+        r[k] = make_int4(u, v, (int32_t)(uint32_t)idx, (int32_t)f);
+        int lo = 0, hi = IEB_B;  // last bucket with bnd[lo] <= v - c_a
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (bnd[mid] <= v - c_a) lo = mid; else hi = mid;
+        }
+        bk[k] = lo;
+        lr[k] = atomicAdd(&cnt[lo], 1u);
+      }
+    }
+    __syncthreads();
+    unsigned total = 0;
+    const unsigned c = cnt[threadIdx.x];
+    loff[threadIdx.x] = block_exclusive_scan<unsigned, IEB_NT>(c, scan_tmp, &total);
+    if (c) gbase[threadIdx.x] = bstart[threadIdx.x] + atomicAdd(&bcur[threadIdx.x], c);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (bk[k] >= 0) {
+        const unsigned slot = loff[bk[k]] + lr[k];
+        stage[slot] = r[k];
+        sb[slot] = (uint16_t)bk[k];
+      }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += IEB_NT) {
+      const int b = sb[i];
+      tmp[e0 + (int64_t)gbase[b] + (i - (int)loff[b])] = stage[i];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_ieb_place(const InEdge *__restrict__ tmp, const int64_t *__restrict__ rowptr,
+                            const int32_t *__restrict__ cuts, int a, unsigned *__restrict__ cursor,
+                            InEdge *__restrict__ rec) {
+  const int32_t c_a = cuts[a];
+  const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts[a + 1]];
+  constexpr int ILP = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < e1; x += stride * ILP) {
+    InEdge r[ILP];
+    unsigned pos[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k)
+      if (x + k * stride < e1) r[k] = tmp[x + k * stride];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k)
+      if (x + k * stride < e1) pos[k] = atomicAdd(&cursor[r[k].y - c_a], 1u);
+#pragma unroll
+    for (int k = 0; k < ILP; ++k)
+      if (x + k * stride < e1) rec[e0 + (int64_t)pos[k]] = r[k];
+  }
+}
+
 // The split table of the resident blocks: for row u of part a (sorted,
 // every entry above u, so in blocks a..p-1), the CSR positions where its runs
 // in blocks a, a+1, ..., p-1 start, then its end.
@@ -497,6 +628,14 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
     uint64_t *scan = nullptr;
     PLAN_TRY(scratch.get(&hist, n + 1));
     PLAN_TRY(scratch.get(&scan, n + 1));
+    // bucket tables of the two-phase build (large parts only)
+    int32_t *ieb_bnd = nullptr;
+    unsigned *ieb_bstart = nullptr, *ieb_bcur = nullptr;
+    if (m / p >= IEB_MIN_EDGES) {
+      PLAN_TRY(scratch.get(&ieb_bnd, IEB_B + 1));
+      PLAN_TRY(scratch.get(&ieb_bstart, IEB_B + 1));
+      PLAN_TRY(scratch.get(&ieb_bcur, IEB_B));
+    }
     for (int a = 0; a < p; ++a) {
       const int64_t bins = n - pl.h_cuts[a];
       if (cudaMemsetAsync(hist, 0, sizeof(unsigned) * (size_t)(bins + 1), s) != cudaSuccess) {
@@ -524,7 +663,37 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
                                                reinterpret_cast<const unsigned long long *>(scan),
                                                bins, pl.boff);
       PLAN_TRY(launch_status("build_plan"));
-      if (m > 0)
+      // large parts: partition into destination buckets, then place (the
+      // temporary array takes 16 bytes per edge of the part); else, or when it
+      // does not fit, one direct scatter
+      InEdge *ieb_tmp = nullptr;
+      const bool two_phase = m / p >= IEB_MIN_EDGES && bins > IEB_B && ieb_bnd &&
+                             dalloc_n(&ieb_tmp, m, s) == BBTC_OK;
+      if (!two_phase) clear_error();
+      if (two_phase) {
+        k_ieb_bounds<<<(IEB_B + 1 + 127) / 128, 128, 0, s>>>(g->rowptr, pl.cuts, a, scan, bins,
+                                                            ieb_bnd, ieb_bstart, ieb_bcur);
+        bbtc_status lst = launch_status("build_plan");
+        if (lst == BBTC_OK &&
+            cudaFuncSetAttribute(k_ieb_partition, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(InEdge) * IEB_T)) != cudaSuccess) {
+          set_error("build_plan: configuring the in-edge partition kernel failed");
+          lst = BBTC_ECUDA;
+        }
+        if (lst == BBTC_OK) {
+          k_ieb_partition<<<(unsigned)num_sms() * 2, IEB_NT, sizeof(InEdge) * IEB_T, s>>>(
+              g->rowptr, g->colidx, g->esrc, pl.cuts, a, p, pl.spl + pl.h_spl_off[a], ieb_bnd,
+              ieb_bstart, ieb_bcur, ieb_tmp);
+          lst = launch_status("build_plan");
+        }
+        if (lst == BBTC_OK) {
+          k_ieb_place<<<grid_for(m / p + 1, 256, 8), 256, 0, s>>>(ieb_tmp, g->rowptr, pl.cuts, a,
+                                                                  hist, pl.ie);
+          lst = launch_status("build_plan");
+        }
+        dfree(ieb_tmp, s);
+        PLAN_TRY(lst);
+      } else if (m > 0) {
         for (int64_t v_lo = pl.h_cuts[a]; v_lo < n; v_lo += IE_SLAB) {
           const int64_t v_hi = v_lo + IE_SLAB < n ? v_lo + IE_SLAB : n;
           k_inedge_scatter<<<ie_grid, IE_NT_S, 0, s>>>(g->rowptr, g->colidx, g->esrc, pl.cuts, a,
@@ -532,6 +701,7 @@ bbtc_status build_plan(bbtc_graph *g, int p, int kernel_mode, int hash_threshold
                                                         hist, pl.ie);
           PLAN_TRY(launch_status("build_plan"));
         }
+      }
     }
   }
 
