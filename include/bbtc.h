@@ -106,6 +106,13 @@ typedef struct {
                                    triangles that contain it; the input of k-truss, Sec. 1),
                                    in the order of bbtc_graph_get_oriented's colidx. Resident
                                    counts only (device_budget_bytes = 0) */
+  const uint8_t *task_mask;     /* NULL, or bbtc_num_tasks(p) bytes (host), one per task in
+                                   Alg. 4 order: only the tasks with a nonzero byte are
+                                   counted, and the total (and the optional outputs) cover
+                                   those tasks alone. The tasks are independent (Sec. 4.2),
+                                   so ranks that count disjoint shares of them sum to the
+                                   whole count (the multi-GPU form of Alg. 7 / Alg. 9).
+                                   bbtc_count and budgeted counts only */
 } bbtc_opts;
 
 #define BBTC_OUT_DEVICE 0x1u
@@ -264,7 +271,7 @@ bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *count_dev,
  * bbtc_graph_get_plan), and every output is a DEVICE pointer: total_dev (one
  * uint64), opts->per_task_out and opts->per_graph_out (nullable;
  * opts->flags must include BBTC_OUT_DEVICE when they are set);
- * opts->per_vertex_out must be NULL. Because it only enqueues kernels and
+ * opts->per_vertex_out and opts->task_mask must be NULL. Because it only enqueues kernels and
  * copies on one stream, the call can be captured into a CUDA graph and
  * replayed. The handle's plan scratch is shared by its calls: calls on one
  * handle must not overlap on the GPU. opts->timeout_ms is ignored.

@@ -60,6 +60,7 @@ class bbtc_opts(ctypes.Structure):
         ("partition", ctypes.c_int32),
         ("per_task_cycles_out", ctypes.c_void_p),
         ("per_edge_out", ctypes.c_void_p),
+        ("task_mask", ctypes.c_void_p),
     ]
 
 
@@ -222,7 +223,7 @@ def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
               device_budget_bytes: int = 0, per_vertex_out=None, per_task_out=None,
               stream=None, hash_threshold: int = 0, per_graph_out=None,
               chunk: int = 0, per_task_cycles_out=None, per_edge_out=None,
-              partition: str | int = "edges") -> bbtc_opts:
+              partition: str | int = "edges", task_mask=None) -> bbtc_opts:
     o = bbtc_opts_init()
     o.partition = PARTITIONS[partition] if isinstance(partition, str) else int(partition)
     o.p = p
@@ -244,11 +245,14 @@ def make_opts(p: int = 0, kernel: str | int = "auto", timeout_ms: int = 0,
     o.per_edge_out = outs[4][0][0] or None
     o.flags = OUT_DEVICE if kinds == {True} else 0
     o.stream = _stream_ptr(stream) or None
+    if task_mask is not None:  # host bytes, one per task in Alg. 4 order
+        task_mask = np.ascontiguousarray(task_mask, dtype=np.uint8)
+        o.task_mask = task_mask.ctypes.data
     # the struct holds raw pointers: keep the output arrays (and the stream) alive
     # for as long as the options are, so a temporary passed here is not freed
     # before the library writes into it
     o._keep = (per_vertex_out, per_task_out, per_graph_out, per_task_cycles_out,
-               per_edge_out, stream)
+               per_edge_out, stream, task_mask)
     return o
 
 

@@ -385,10 +385,16 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
     BBTC_CUDA(cudaMemsetAsync(edge_sup, 0, sizeof(unsigned) * (size_t)(g->m > 0 ? g->m : 1), s));
   }
   const bool per_graph = opts.per_graph_out != nullptr;
+  uint8_t *task_mask = nullptr;  // this caller's share of the tasks, on the device
+  if (opts.task_mask) {
+    BBTC_TRY(scratch.get(&task_mask, pl.ntasks));
+    BBTC_CUDA(cudaMemcpyAsync(task_mask, opts.task_mask, (size_t)pl.ntasks,
+                              cudaMemcpyHostToDevice, s));
+  }
   if (budgeted) {
     StreamStats st;
     BBTC_TRY(run_count_streamed(g, g->plan, opts.device_budget_bytes, vertex_count, per_graph,
-                                opts.timeout_ms, s, &st, task_cycles));
+                                opts.timeout_ms, s, &st, task_cycles, task_mask));
     g->stream_stats.rounds = st.rounds;
     g->stream_stats.h2d_bytes = st.h2d_bytes;
     g->stream_stats.copy_ms = st.copy_ms;
@@ -398,7 +404,7 @@ bbtc_status bbtc_count(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t *count
     g->stream_stats_total_ms = st.total_ms;
   } else {
     BBTC_TRY(run_count(g, pl, vertex_count, per_graph, opts.timeout_ms, s, g->ev[4], g->ev[5],
-                       task_cycles, edge_sup));
+                       task_cycles, edge_sup, task_mask));
     g->stream_stats_total_ms = -1.0;
   }
   unsigned long long head[SCR_TASKS] = {0, 0, 0};
@@ -448,10 +454,10 @@ bbtc_status bbtc_count_async(bbtc_graph_t g, const bbtc_opts *opts_in, uint64_t 
               "with bbtc_count (without a device budget) or bbtc_graph_get_plan first");
     return BBTC_EINVAL;
   }
-  if (opts.per_vertex_out || opts.per_task_cycles_out || opts.per_edge_out ||
+  if (opts.per_vertex_out || opts.per_task_cycles_out || opts.per_edge_out || opts.task_mask ||
       ((opts.per_task_out || opts.per_graph_out) && !(opts.flags & BBTC_OUT_DEVICE))) {
     set_error("bbtc_count_async: outputs must be device pointers (BBTC_OUT_DEVICE) and "
-              "per_vertex_out / per_task_cycles_out / per_edge_out must be NULL");
+              "per_vertex_out / per_task_cycles_out / per_edge_out / task_mask must be NULL");
     return BBTC_EINVAL;
   }
   DeviceGuard dg(g->device);

@@ -37,6 +37,7 @@ struct CountParams {
   unsigned long long *graph_count;  // per-graph counts (MODE & 2)
   unsigned long long *task_cycles;  // nullable: SM cycles spent on each task's items
   unsigned *edge_sup;               // per-edge support by position in the block columns (MODE & 4)
+  const uint8_t *task_mask;         // nullable: items of tasks whose byte is 0 are skipped
   int32_t *status;
   uint64_t timeout_ns;
 };
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(CT_NT, 3) k_count(CountParams P) {
     }
     const WorkItem w = P.items[it];
     const int t = w.task;
+    if (P.task_mask && P.task_mask[t] == 0) continue;  // another rank's task
     const long long t_item = P.task_cycles ? clock64() : 0;
     const int kflag = w.flags & 3;  // 0 INTERSECT, 1 HASHMAP, 2 AUTO (per list)
     const int hash_min = w.flags >> 2;  // AUTO: longer lists hash, shorter ones sorted
@@ -825,7 +827,8 @@ bbtc_status count_reset(bbtc_graph *g, const Plan &pl, unsigned long long *verte
 
 bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t nitems,
                          unsigned long long *vertex_count, bool per_graph, uint32_t timeout_ms,
-                         cudaStream_t s, unsigned long long *task_cycles, unsigned *edge_sup) {
+                         cudaStream_t s, unsigned long long *task_cycles, unsigned *edge_sup,
+                         const uint8_t *task_mask) {
   if (nitems <= 0) return BBTC_OK;
   unsigned long long *scr = pl.scratch;
   BBTC_CUDA(cudaMemsetAsync(scr + SCR_HEAD, 0, sizeof(unsigned long long), s));
@@ -842,6 +845,7 @@ bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t n
   P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
   P.task_cycles = task_cycles;
   P.edge_sup = edge_sup;
+  P.task_mask = task_mask;
   const int mode = (vertex_count ? MODE_VERTEX : 0) | (per_graph ? MODE_GRAPH : 0) |
                    (edge_sup ? MODE_EDGE : 0);
   int64_t blocks = (int64_t)num_sms() * pl.blocks_per_sm[mode];
@@ -882,11 +886,12 @@ bbtc_status count_finish(const Plan &pl, cudaStream_t s) {
 bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                       bool per_graph, uint32_t timeout_ms, cudaStream_t s,
                       cudaEvent_t ev_begin, cudaEvent_t ev_end,
-                      unsigned long long *task_cycles, unsigned *edge_sup) {
+                      unsigned long long *task_cycles, unsigned *edge_sup,
+                      const uint8_t *task_mask) {
   BBTC_TRY(count_reset(g, pl, vertex_count, per_graph, s));
   if (ev_begin) BBTC_CUDA(cudaEventRecord(ev_begin, s));
   BBTC_TRY(count_launch(g, pl, 0, pl.nitems, vertex_count, per_graph, timeout_ms, s,
-                        task_cycles, edge_sup));
+                        task_cycles, edge_sup, task_mask));
   if (ev_end) BBTC_CUDA(cudaEventRecord(ev_end, s));
   return count_finish(pl, s);
 }
@@ -979,6 +984,7 @@ bbtc_status count_plans(bbtc_graph *const *gs, int32_t ng, uint32_t timeout_ms, 
     P.graph_count = nullptr;
     P.task_cycles = nullptr;
     P.edge_sup = nullptr;
+    P.task_mask = nullptr;
     P.status = reinterpret_cast<int32_t *>(counters + 1);
     P.timeout_ns = (uint64_t)timeout_ms * 1000000ull;
     if (blocks_per_sm < 1) BBTC_TRY(configure_mode<0>(&blocks_per_sm));
@@ -1104,6 +1110,7 @@ extern "C" bbtc_status bbtc_count_noalloc(bbtc_graph_t g, int32_t p, uint64_t *c
       P.graph_count = nullptr;
       P.task_cycles = nullptr;
       P.edge_sup = nullptr;
+      P.task_mask = nullptr;
       P.status = reinterpret_cast<int32_t *>(scratch + NOALLOC_STATUS);
       P.timeout_ns = 0;
       const size_t smem = count_smem_bytes();

@@ -178,15 +178,18 @@ bbtc_status configure_count_kernels(Plan *pl);
 bbtc_status run_count(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                       bool per_graph, uint32_t timeout_ms, cudaStream_t s,
                       cudaEvent_t ev_begin, cudaEvent_t ev_end,
-                      unsigned long long *task_cycles = nullptr, unsigned *edge_sup = nullptr);
+                      unsigned long long *task_cycles = nullptr, unsigned *edge_sup = nullptr,
+                      const uint8_t *task_mask = nullptr);
 // The three parts of run_count: zero the outputs, drain items [item0,
 // item0 + nitems) in one persistent launch (accumulating), sum the tasks.
 bbtc_status count_reset(bbtc_graph *g, const Plan &pl, unsigned long long *vertex_count,
                         bool per_graph, cudaStream_t s);
+// task_mask (device, nullable): one byte per task; items of tasks whose byte is
+// zero are skipped.
 bbtc_status count_launch(bbtc_graph *g, const Plan &pl, int64_t item0, int64_t nitems,
                          unsigned long long *vertex_count, bool per_graph, uint32_t timeout_ms,
                          cudaStream_t s, unsigned long long *task_cycles = nullptr,
-                         unsigned *edge_sup = nullptr);
+                         unsigned *edge_sup = nullptr, const uint8_t *task_mask = nullptr);
 bbtc_status count_finish(const Plan &pl, cudaStream_t s);
 // The error of a nonzero status word left by the counting kernel: 1 = it
 // passed opts.timeout_ms (ETIMEOUT), 2 = a bulk copy wait ran out (EINTERNAL).
@@ -216,7 +219,8 @@ struct StreamStats {
 bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
                                unsigned long long *vertex_count, bool per_graph,
                                uint32_t timeout_ms, cudaStream_t s, StreamStats *stats,
-                               unsigned long long *task_cycles = nullptr);
+                               unsigned long long *task_cycles = nullptr,
+                               const uint8_t *task_mask = nullptr);
 
 // Work figures of the oriented graph (device): sum_{(u,v)} d+(v) and
 // sum_u d+(u)(d+(u)-1)/2.

@@ -164,7 +164,7 @@ void free_plan_host(Plan *pl) {
 bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
                                unsigned long long *vertex_count, bool per_graph,
                                uint32_t timeout_ms, cudaStream_t s, StreamStats *stats,
-                               unsigned long long *task_cycles) {
+                               unsigned long long *task_cycles, const uint8_t *task_mask) {
   const int p = pl.p;
   const int64_t nt = pl.ntasks;
   BBTC_TRY(plan_to_host(g, pl, g->m, s));
@@ -366,7 +366,8 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
           break;
         }
         st = count_launch(g, pl, runs[gpos].item0, runs[gend - 1].item1 - runs[gpos].item0,
-                          vertex_count, per_graph, timeout_ms, s, task_cycles);
+                          vertex_count, per_graph, timeout_ms, s, task_cycles, nullptr,
+                          task_mask);
         if (st != BBTC_OK) break;
         if (cudaEventRecord(kern_done[h], s) != cudaSuccess) {
           st = BBTC_ECUDA;
@@ -538,7 +539,7 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
         break;
       }
       st = count_launch(g, pl, runs[first].item0, runs[pos - 1].item1 - runs[first].item0,
-                        vertex_count, per_graph, timeout_ms, s, task_cycles);
+                        vertex_count, per_graph, timeout_ms, s, task_cycles, nullptr, task_mask);
       if (st != BBTC_OK) break;
       if (cudaEventRecord(kern_done[h], s) != cudaSuccess) {
         st = BBTC_ECUDA;
