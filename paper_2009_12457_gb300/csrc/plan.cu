@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(IE_NT_S) k_inedge_scatter(const int64_t *__res
 //  2. place: a grid-stride pass reads the temporary array in order and puts
 //     each record at its destination's cursor. The CTAs move through the
 //     buckets together, so the bucket being filled (tens of MB) and its
-//     cursors stay in L2 and its lines go to HBM once, whole.
+//     cursors stay in L2 and its lines go to HBM once, whole; the temporary
+//     array is streamed with evict-first loads so it does not displace them.
 constexpr int IEB_T = 4096;   // edges per partition tile
 constexpr int IEB_NT = 512;   // threads of a partition CTA (8 edges each)
 constexpr int IEB_B = 512;    // buckets (one per partition thread in the scan)
@@ -252,11 +253,34 @@ __global__ void __launch_bounds__(IEB_NT, 2)
   const int32_t c_a = cuts_g[a];
   const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts_g[a + 1]];
   __syncthreads();
-  for (int64_t t0 = e0 + (int64_t)blockIdx.x * IEB_T; t0 < e1; t0 += (int64_t)gridDim.x * IEB_T) {
+  // the (v, u) of the next tile's edges are loaded while this tile is bucketed
+  int32_t pv[8], pu[8];
+  const int64_t tstep = (int64_t)gridDim.x * IEB_T;
+  auto load_tile = [&](int64_t tt0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t idx = tt0 + (int)threadIdx.x + k * IEB_NT;
+      pv[k] = 0;
+      pu[k] = 0;
+      if (idx < e1) {
+        pv[k] = colidx[idx];
+        pu[k] = esrc[idx];
+      }
+    }
+  };
+  load_tile(e0 + (int64_t)blockIdx.x * IEB_T);
+  for (int64_t t0 = e0 + (int64_t)blockIdx.x * IEB_T; t0 < e1; t0 += tstep) {
     const int nv = (int)(e1 - t0 < IEB_T ? e1 - t0 : IEB_T);
+    int32_t cv[8], cu[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      cv[k] = pv[k];
+      cu[k] = pu[k];
+    }
+    load_tile(t0 + tstep);
     cnt[threadIdx.x] = 0;
     __syncthreads();
-    InEdge r[8];
+    uint32_t fk[8];
     int bk[8];
     unsigned lr[8];
 #pragma unroll
@@ -264,12 +288,11 @@ __global__ void __launch_bounds__(IEB_NT, 2)
       const int i = (int)threadIdx.x + k * IEB_NT;
       bk[k] = -1;
       if (i < nv) {
-        const int64_t idx = t0 + i;
-        const int32_t v = colidx[idx];
-        const int32_t u = esrc[idx];
+        const int32_t v = cv[k];
+        const int32_t u = cu[k];
         const int b = part_of_dev(cuts, p, v);  // >= a: v > u
         const uint32_t f = spl_a[(int64_t)(u - c_a) * (p - a + 1) + (b - a + 1)];
-        r[k] = make_int4(u, v, (int32_t)(uint32_t)idx, (int32_t)f);
+        fk[k] = f;
         int lo = 0, hi = IEB_B;  // last bucket with bnd[lo] <= v - c_a
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
@@ -289,7 +312,8 @@ __global__ void __launch_bounds__(IEB_NT, 2)
     for (int k = 0; k < 8; ++k)
       if (bk[k] >= 0) {
         const unsigned slot = loff[bk[k]] + lr[k];
-        stage[slot] = r[k];
+        const int64_t idx = t0 + (int)threadIdx.x + k * IEB_NT;  // the edge's CSR position
+        stage[slot] = make_int4(cu[k], cv[k], (int32_t)(uint32_t)idx, (int32_t)fk[k]);
         sb[slot] = (uint16_t)bk[k];
       }
     __syncthreads();
@@ -313,7 +337,7 @@ __global__ void k_ieb_place(const InEdge *__restrict__ tmp, const int64_t *__res
     unsigned pos[ILP];
 #pragma unroll
     for (int k = 0; k < ILP; ++k)
-      if (x + k * stride < e1) r[k] = tmp[x + k * stride];
+      if (x + k * stride < e1) r[k] = __ldcs(tmp + x + k * stride);  // read once: evict first
 #pragma unroll
     for (int k = 0; k < ILP; ++k)
       if (x + k * stride < e1) pos[k] = atomicAdd(&cursor[r[k].y - c_a], 1u);
