@@ -210,6 +210,7 @@ constexpr int IEB_T = 4096;   // edges per partition tile
 constexpr int IEB_NT = 512;   // threads of a partition CTA (8 edges each)
 constexpr int IEB_B = 512;    // buckets (one per partition thread in the scan)
 constexpr int64_t IEB_MIN_EDGES = 16ll << 20;  // smaller parts use the direct scatter
+constexpr int IEB_LUT = 4096;  // entries of the partition's bucket lookup table
 static_assert(IEB_NT == IEB_B && IEB_T == 8 * IEB_NT, "partition layout");
 
 // Bucket b of part a holds the destinations [bnd[b], bnd[b+1]) (relative to
@@ -246,12 +247,27 @@ __global__ void __launch_bounds__(IEB_NT, 2)
   __shared__ unsigned scan_tmp[IEB_NT / 32 + 1];
   __shared__ int32_t cuts[MAXP + 1];
   __shared__ uint16_t sb[IEB_T];  // bucket of each staged slot
+  // lut[k]: the bucket holding destination offset k << shift; a destination
+  // in [k << shift, (k + 1) << shift) lies in buckets lut[k] .. lut[k + 1]
+  __shared__ uint16_t lut[IEB_LUT + 1];
   extern __shared__ __align__(16) unsigned char ieb_smem[];
   InEdge *stage = reinterpret_cast<InEdge *>(ieb_smem);  // IEB_T records
   for (int i = threadIdx.x; i <= IEB_B; i += IEB_NT) bnd[i] = bnd_g[i];
   for (int i = threadIdx.x; i <= p; i += IEB_NT) cuts[i] = cuts_g[i];
   const int32_t c_a = cuts_g[a];
   const int64_t e0 = rowptr[c_a], e1 = rowptr[cuts_g[a + 1]];
+  __syncthreads();
+  int shift = 0;
+  while (((int64_t)IEB_LUT << shift) < (int64_t)bnd[IEB_B]) ++shift;
+  for (int k = threadIdx.x; k <= IEB_LUT; k += IEB_NT) {
+    const int64_t x = (int64_t)k << shift;
+    int lo = 0, hi = IEB_B;  // last bucket with bnd[lo] <= x
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (bnd[mid] <= x) lo = mid; else hi = mid;
+    }
+    lut[k] = (uint16_t)lo;
+  }
   __syncthreads();
   // the (v, u) of the next tile's edges are loaded while this tile is bucketed
   int32_t pv[8], pu[8];
@@ -293,10 +309,11 @@ __global__ void __launch_bounds__(IEB_NT, 2)
         const int b = part_of_dev(cuts, p, v);  // >= a: v > u
         const uint32_t f = spl_a[(int64_t)(u - c_a) * (p - a + 1) + (b - a + 1)];
         fk[k] = f;
-        int lo = 0, hi = IEB_B;  // last bucket with bnd[lo] <= v - c_a
+        const int32_t x = v - c_a;
+        int lo = lut[x >> shift], hi = lut[(x >> shift) + 1] + 1;  // last bucket with bnd[lo] <= x
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
-          if (bnd[mid] <= v - c_a) lo = mid; else hi = mid;
+          if (bnd[mid] <= x) lo = mid; else hi = mid;
         }
         bk[k] = lo;
         lr[k] = atomicAdd(&cnt[lo], 1u);

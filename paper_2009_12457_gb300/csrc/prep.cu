@@ -290,7 +290,8 @@ __global__ void k_tile_rows(const int64_t *__restrict__ rowptr, int64_t n, int64
 // of a row are added once per thread. MODE 0:
 // degree of u += first copies of v != u, flag unsorted rows and out-of-range
 // ids. MODE 1: out-degree at rank(u) += first copies with rank(v) > rank(u).
-// MODE 2: scatter rank(v) into row rank(u) (any order; rows are sorted after).
+// MODE 2: scatter rank(v) into row rank(u) (any order; rows are sorted after;
+// the rows' sources are written afterwards by k_fill_esrc, with coalesced stores).
 // When rr is given, MODE 1 also stores each entry's rank(v) when the entry is
 // such an upward first copy (else -1), and MODE 2 reads it back in order
 // instead of gathering rank(v) a second time.
@@ -307,7 +308,6 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
                                                     const int64_t *__restrict__ rowptr_o,
                                                     unsigned int *__restrict__ cursor,
                                                     int32_t *__restrict__ colidx_o,
-                                                    int32_t *__restrict__ esrc_o,
                                                     int32_t *__restrict__ err,
                                                     const int64_t *__restrict__ voff, int ng,
                                                     int32_t *__restrict__ rr) {
@@ -339,11 +339,13 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
     // equal keys form one group per row and each group costs one atomic.
     int64_t key[SP_ITEMS];
     int32_t val[SP_ITEMS];  // MODE 2: rank(v)
+    int32_t up[SP_ITEMS];   // MODE 1: the entry's upward rank, else -1 (stored in rr)
 #pragma unroll
     for (int i = 0; i < SP_ITEMS; ++i) {
       const int64_t e = first + i;
       key[i] = -1;
       val[i] = 0;
+      up[i] = -1;
       if (e < t1) {
         while (e >= row_end) {  // next non-empty row
           ++u;
@@ -381,8 +383,20 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
           const int32_t rv = head ? rank[v] : -1;
           if (head && rv > ru) key[i] = ru;
           val[i] = rv;
-          if (MODE == 1 && rr) rr[e] = head && rv > ru ? rv : -1;
+          if (MODE == 1) up[i] = head && rv > ru ? rv : -1;
         }
+      }
+    }
+    if (MODE == 1 && rr) {
+      // rr + first is 32-byte aligned (first is a multiple of 8 entries)
+      if (first + SP_ITEMS <= t1) {
+        int4 *d = reinterpret_cast<int4 *>(rr + first);
+        d[0] = make_int4(up[0], up[1], up[2], up[3]);
+        d[1] = make_int4(up[4], up[5], up[6], up[7]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < SP_ITEMS; ++i)
+          if (first + i < t1) rr[first + i] = up[i];
       }
     }
     if (MODE < 2) {
@@ -427,10 +441,36 @@ __global__ void __launch_bounds__(SP_NT) k_sym_pass(const int64_t *__restrict__ 
             pos = rowptr_o[cur] + (int64_t)atomicAdd(&cursor[cur], c);
           }
           colidx_o[pos] = val[i];
-          esrc_o[pos] = (int32_t)cur;
           ++pos;
         }
       }
+    }
+  }
+}
+
+// esrc[x] = the row of position x, for every position of the oriented CSR.
+// A warp takes 32 rows: lane j holds the start of row r0 + j, and each
+// position of the rows' span finds its row by a search over the lanes, so
+// the stores are coalesced whatever the row lengths.
+__global__ void k_fill_esrc(const int64_t *__restrict__ rowptr, int64_t n,
+                            int32_t *__restrict__ esrc) {
+  const unsigned lane = threadIdx.x & 31u;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; r0 < n;
+       r0 += nwarps * 32) {
+    const int64_t rj = r0 + lane < n ? r0 + lane : n;
+    const int64_t start_j = rowptr[rj];
+    const int64_t span_end = rowptr[r0 + 32 < n ? r0 + 32 : n];
+    const int64_t span_start = __shfl_sync(0xffffffffu, start_j, 0);
+    for (int64_t x0 = span_start; x0 < span_end; x0 += 32) {
+      const int64_t x = x0 + lane;
+      int j = 0;  // last lane whose row starts at or before x
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int64_t sj = __shfl_sync(0xffffffffu, start_j, j + step);
+        if (sj <= x) j += step;
+      }
+      if (x < span_end) esrc[x] = (int32_t)(r0 + j);
     }
   }
 }
@@ -645,8 +685,8 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   BBTC_LAUNCH_CHECK();
   const unsigned grid = grid_for(ntiles, 1, 32);
   k_sym_pass<0><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, g->deg, nullptr,
-                                       nullptr, nullptr, nullptr, nullptr, nullptr, err, g->voff,
-                                       g->ng, nullptr);
+                                       nullptr, nullptr, nullptr, nullptr, err, g->voff, g->ng,
+                                       nullptr);
   BBTC_LAUNCH_CHECK();
   int32_t herr = 0;
   BBTC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -708,7 +748,7 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   } free_rr{rr, s};
   k_sym_pass<1><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, nullptr, rank,
                                        reinterpret_cast<unsigned long long *>(g->rowptr),
-                                       nullptr, nullptr, nullptr, nullptr, err, g->voff, g->ng, rr);
+                                       nullptr, nullptr, nullptr, err, g->voff, g->ng, rr);
   BBTC_LAUNCH_CHECK();
   int64_t *stats = nullptr;
   BBTC_TRY(scratch.get(&stats, 2));
@@ -733,9 +773,13 @@ static bbtc_status prepare_sym_sorted(bbtc_graph *g, const int64_t *d_rowptr,
   BBTC_TRY(scratch.get(&cursor, n));
   BBTC_CUDA(cudaMemsetAsync(cursor, 0, sizeof(unsigned int) * (size_t)(n > 0 ? n : 1), s));
   k_sym_pass<2><<<grid, SP_NT, 0, s>>>(d_rowptr, d_colidx, n, nnz, tile_rows, nullptr, rank,
-                                       nullptr, g->rowptr, cursor, g->colidx, g->esrc, err,
-                                       g->voff, g->ng, rr);
+                                       nullptr, g->rowptr, cursor, g->colidx, err, g->voff, g->ng,
+                                       rr);
   BBTC_LAUNCH_CHECK();
+  if (m > 0) {
+    k_fill_esrc<<<grid_for((n + 31) / 32 * 32, 256, 16), 256, 0, s>>>(g->rowptr, n, g->esrc);
+    BBTC_LAUNCH_CHECK();
+  }
   if (m > 0) {
     if (g->dplus_max <= SEG_CAP) {
       k_sort_rows<<<grid_for((n + 31) / 32, SR_WARPS, 64), SR_WARPS * 32, 0, s>>>(g->rowptr, n,
