@@ -6,6 +6,8 @@
 
 #include <mutex>
 #include <new>
+#include <unordered_map>
+#include <vector>
 
 #include "graph.cuh"
 #include "primitives.cuh"
@@ -39,6 +41,61 @@ void set_error(const char *fmt, ...) {
 
 void clear_error() { g_error[0] = '\0'; }
 
+// Large blocks (at least kCacheMin bytes) are not returned to the pool when
+// freed: an idle block is kept, with an event marking the end of its last use,
+// and handed out again for a request of up to its size (and at least 4/5 of
+// it) on a stream that first waits for that event. A repeated call with the
+// same sizes then gets back the same blocks: taking a fresh block of tens of
+// GB from the pool costs about a millisecond per GB of host time, during which
+// the GPU runs dry. Idle blocks are released to the pool when an allocation
+// fails, before a budgeted (streamed) count, and when they would exceed half
+// of the device's memory.
+namespace {
+constexpr size_t kCacheMin = 64ull << 20;
+struct IdleBlock {
+  void *p;
+  size_t bytes;
+  cudaEvent_t ev;
+};
+struct BlockCache {
+  std::mutex mu;
+  std::vector<IdleBlock> idle[64];
+  std::unordered_map<void *, size_t> live[64];  // large blocks handed out: bytes
+  uint64_t idle_bytes[64] = {};
+  uint64_t cap[64] = {};
+};
+BlockCache &block_cache() {
+  static BlockCache *c = new BlockCache;  // never destroyed: blocks outlive static teardown
+  return *c;
+}
+
+// frees the idle blocks of device dev (caller holds the lock), after s waits for
+// their last use
+void release_idle_locked(BlockCache &c, int dev, cudaStream_t s) {
+  for (IdleBlock &b : c.idle[dev]) {
+    cudaStreamWaitEvent(s, b.ev, 0);
+    cudaFreeAsync(b.p, s);
+    cudaEventDestroy(b.ev);
+  }
+  c.idle[dev].clear();
+  c.idle_bytes[dev] = 0;
+}
+}  // namespace
+
+void release_cached_blocks(int dev, cudaStream_t s) {
+  if (dev < 0 || dev >= 64) return;
+  BlockCache &c = block_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  release_idle_locked(c, dev, s);
+}
+
+uint64_t cached_block_bytes(int dev) {
+  if (dev < 0 || dev >= 64) return 0;
+  BlockCache &c = block_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  return c.idle_bytes[dev];
+}
+
 bbtc_status dalloc(void **p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   int dev = 0;
@@ -53,19 +110,87 @@ bbtc_status dalloc(void **p, size_t bytes, cudaStream_t s) {
         uint64_t threshold = ~0ull;  // keep freed blocks cached for the next call
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
       }
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) block_cache().cap[dev] = total_b / 2;
+      cudaGetLastError();
     });
+  const bool large = bytes >= kCacheMin && dev >= 0 && dev < 64;
+  if (large) {
+    BlockCache &c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    std::vector<IdleBlock> &v = c.idle[dev];
+    int best = -1;  // the smallest fitting block, one whose last use has ended first
+    bool best_done = false;
+    for (int i = 0; i < (int)v.size(); ++i) {
+      if (v[i].bytes < bytes || v[i].bytes - bytes > v[i].bytes / 5) continue;
+      const bool done = cudaEventQuery(v[i].ev) == cudaSuccess;
+      if (best < 0 || (done && !best_done) ||
+          (done == best_done && v[i].bytes < v[best].bytes)) {
+        best = i;
+        best_done = done;
+      }
+    }
+    cudaGetLastError();
+    if (best >= 0) {
+      IdleBlock b = v[best];
+      v.erase(v.begin() + best);
+      c.idle_bytes[dev] -= b.bytes;
+      cudaStreamWaitEvent(s, b.ev, 0);
+      cudaEventDestroy(b.ev);
+      c.live[dev][b.p] = b.bytes;
+      *p = b.p;
+      return BBTC_OK;
+    }
+  }
   cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e == cudaErrorMemoryAllocation && dev >= 0 && dev < 64) {
+    cudaGetLastError();
+    bool retry = false;
+    {
+      BlockCache &c = block_cache();
+      std::lock_guard<std::mutex> lk(c.mu);
+      retry = !c.idle[dev].empty();
+      release_idle_locked(c, dev, s);
+    }
+    if (retry) e = cudaMallocAsync(p, bytes, s);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? BBTC_ENOMEM : BBTC_ECUDA;
   }
+  if (large) {
+    BlockCache &c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.live[dev][*p] = bytes;
+  }
   return BBTC_OK;
 }
 
 void dfree(void *p, cudaStream_t s) {
-  if (p) cudaFreeAsync(p, s);
+  if (!p) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+    BlockCache &c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.live[dev].find(p);
+    if (it != c.live[dev].end()) {
+      const size_t bytes = it->second;
+      c.live[dev].erase(it);
+      cudaEvent_t ev = nullptr;
+      if (c.idle_bytes[dev] + bytes <= c.cap[dev] &&
+          cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+          cudaEventRecord(ev, s) == cudaSuccess) {
+        c.idle[dev].push_back(IdleBlock{p, bytes, ev});
+        c.idle_bytes[dev] += bytes;
+        return;
+      }
+      if (ev) cudaEventDestroy(ev);
+      cudaGetLastError();
+    }
+  }
+  cudaFreeAsync(p, s);
 }
 
 }  // namespace bbtc
@@ -624,6 +749,10 @@ bbtc_status bbtc_device_memory(int32_t device, uint64_t *available, uint64_t *to
   uint64_t reserved = 0, used = 0;
   BBTC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
   BBTC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  // idle blocks kept by the library's cache are part of the pool's used bytes
+  // but are handed out again (or released) on demand
+  const uint64_t idle = cached_block_bytes(device);
+  if (idle <= used) used -= idle;
   if (available) *available = (uint64_t)free_b + (reserved > used ? reserved - used : 0);
   if (total) *total = (uint64_t)total_b;
   if (pool_reserved) *pool_reserved = reserved;

@@ -43,8 +43,13 @@ bbtc_status launch_status(const char *where);
 // Stream-ordered device allocation from the device's default memory pool.
 // Blocks stay cached in the pool between calls (release threshold raised at
 // first use), so repeated create/count calls do not pay cudaMalloc.
+// Blocks of 64 MB and more are kept when freed and handed out again for a
+// request of a similar size (see api.cu); release_cached_blocks returns the
+// idle ones of a device to the pool, cached_block_bytes reports their size.
 bbtc_status dalloc(void **p, size_t bytes, cudaStream_t s);
 void dfree(void *p, cudaStream_t s);
+void release_cached_blocks(int dev, cudaStream_t s);
+uint64_t cached_block_bytes(int dev);
 
 template <typename T>
 inline bbtc_status dalloc_n(T **p, int64_t count, cudaStream_t s) {

@@ -168,6 +168,9 @@ bbtc_status run_count_streamed(bbtc_graph *g, Plan &pl, uint64_t budget,
   const int p = pl.p;
   const int64_t nt = pl.ntasks;
   BBTC_TRY(plan_to_host(g, pl, g->m, s));
+  // a budgeted count holds no idle cached blocks: the device memory it uses,
+  // and the high-water mark it reports, are its own
+  release_cached_blocks(g->device, s);
 
   // small plan tables on the host
   std::vector<WorkItem> items((size_t)pl.nitems);
