@@ -321,7 +321,9 @@ typedef struct {
   uint64_t stream_device_peak_bytes; /* last budgeted count: high-water mark of the library's
                                         device memory during the count (the handle's
                                         oriented CSR and plan tables, which stay resident,
-                                        plus the block pool of at most the budget) */
+                                        plus the block pool of at most the budget); the
+                                        library's idle cached blocks are released before
+                                        a budgeted count */
   int32_t stream_mode;        /* last budgeted count: 1 = every block CSR kept on the device
                                  and each in-edge block copied once; 2 = blocks placed round
                                  by round in the pool and re-copied when evicted */
@@ -331,10 +333,12 @@ bbtc_status bbtc_graph_get_timings(bbtc_graph_t g, bbtc_timings *t);
 
 /*
  * Device memory the library can still use on `device` (an ordinal): the free
- * bytes the driver reports plus the bytes that the device's stream-ordered
- * pool holds without using them (the library allocates from that pool and
- * keeps freed blocks there for later calls, so the driver's figure alone
- * undercounts). Any output may be NULL. Used by callers that admit work by
+ * bytes the driver reports, plus the bytes that the device's stream-ordered
+ * pool holds without using them, plus the library's idle cached blocks (the
+ * library allocates from that pool, keeps freed blocks of 64 MB and more for
+ * later calls of a similar size, and releases them when an allocation fails,
+ * so the driver's figure alone undercounts). pool_used excludes the idle
+ * cached blocks. Any output may be NULL. Used by callers that admit work by
  * free device memory, such as the serving loop; the paper has no counterpart.
  * Errors: EINVAL for an unknown device; ECUDA.
  */
