@@ -73,3 +73,33 @@ def test_lpt_masks_partition_and_balance():
     # first 3 -> rank 1 (load 4 < 5); the second 3 -> rank 0 (5 < 7); 2 -> rank 1 (7 < 8)
     masks = shard.lpt_masks([5, 4, 3, 3, 2], 2)
     assert masks[0].tolist() == [1, 0, 0, 1, 0] and masks[1].tolist() == [0, 1, 1, 0, 1]
+
+
+def _rank_shard_count(rank, world, port, ref, out):
+    """shard.shard_count's own steps (plan, estimate, share, count, one sum) on a
+    gloo rank, with the library's calls answered from the oracle's values."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import paper_2009_12457_gb300 as bb
+        planned = []
+        bb.bbtc_graph_plan = lambda h, o: planned.append(o["p"])
+        bb.bbtc_graph_get_plan = lambda h, p: {"exec_time": ref[p][0]}
+        bb.make_opts = lambda **kw: kw
+        bb.bbtc_count = lambda h, o: int(ref[o["p"]][1][np.asarray(o["task_mask"]).astype(bool)].sum())
+        res = {p: shard.shard_count(0, p, rank, world, dist) for p in P_LIST}
+        out[rank] = (res, planned)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_shard_count_over_gloo_ranks(world):
+    ref = _reference()
+    port = 31700 + (os.getpid() % 2000) + world
+    out = mp.Manager().dict()
+    mp.spawn(_rank_shard_count, args=(world, port, ref, out), nprocs=world, join=True)
+    for r in range(world):
+        res, planned = out[r]
+        assert res == {p: ref["total"] for p in P_LIST}
+        assert planned == list(P_LIST)  # the plan is built before its estimate is read
