@@ -685,7 +685,7 @@ def measure(args, workload: str, p: int, budget_gb: float, env, with_cpu: bool):
     # N(u) above v (sum over u of d+(u)(d+(u)-1)/2 elements, 4 B each)
     own = 4 * (5 * m + info["wedges_out"])
     achieved = own / (kms / 1000.0) / 1e9
-    # the survey's W_min: every edge's N(v) read once per in-edge of v; this kernel
+    # W_min: every edge's N(v) read once per in-edge of v; this kernel
     # never makes those reads, so it is reported for context, not as its roofline
     wmin = 4 * (m + info["wedges_in"])
     # bytes a merge-based intersection of both full lists would read:
