@@ -112,7 +112,9 @@ typedef struct {
                                    those tasks alone. The tasks are independent (Sec. 4.2),
                                    so ranks that count disjoint shares of them sum to the
                                    whole count (the multi-GPU form of Alg. 7 / Alg. 9).
-                                   bbtc_count and budgeted counts only */
+                                   Read (copied to the device) during the call; the caller
+                                   keeps it. bbtc_count, resident or budgeted, only:
+                                   bbtc_count_batch ignores it, bbtc_count_async refuses it */
 } bbtc_opts;
 
 #define BBTC_OUT_DEVICE 0x1u

@@ -692,6 +692,7 @@ bbtc_status bbtc_count_batch(const bbtc_graph_t *gs, int32_t ng, const bbtc_opts
       uo.per_vertex_out = nullptr;
       uo.per_task_cycles_out = nullptr;
       uo.per_edge_out = nullptr;
+      uo.task_mask = nullptr;  // the union's tasks are not the caller's
       uo.per_graph_out = sub;
       uo.flags = 0;
       uo.stream = s;
