@@ -87,3 +87,35 @@ def test_partition_option():
     assert bb.make_opts(p=4, partition="edges").partition == 0
     text = open(os.path.join(ROOT, "include", "bbtc.h")).read()
     assert "BBTC_PARTITION_EDGES = 0" in text and "BBTC_PARTITION_PROBE = 1" in text
+
+
+def test_python_struct_offsets_match_the_c_compiler(tmp_path):
+    """Offsets and sizes of the three public structs as gcc lays them out from
+    include/bbtc.h, against the ctypes mirrors the binding passes to the library."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = ("bbtc_opts", "bbtc_graph_info", "bbtc_timings")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bbtc.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'  printf("{s} sizeof %zu\\n", sizeof({s}));')
+        for f in _c_struct_fields(s):
+            lines.append(f'  printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for s in structs:
+        cls = getattr(bb, s)
+        assert got[(s, "sizeof")] == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert got[(s, f)] == getattr(cls, f).offset, (s, f)
